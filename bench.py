@@ -1,0 +1,339 @@
+#!/usr/bin/env python
+"""Throughput of the DI-LBM hot path on one GB300 (MLUPS, HBM roofline).
+
+One step = one time step of the whole hot path on the lattice: the fused
+pull-stream + DI-collide sweep over every node (with the solid fraction and
+the per-tile force partials), the per-particle FP64 force/torque reduction
+with Wan-Turek repulsion, and the rigid-body update with re-binning.
+
+Default workload: 4096 x 4096 periodic box with 2048 free discs (radius
+uniform in [6, 12], rho_s/rho_f = 1.2, g = 1e-6, tau = 0.8, interface width 2),
+FP32 deviation storage.  The populations (1.2 GB for A and B) are far larger
+than L2, so no flush is needed between steps.
+
+Prints one JSON line.  ``--impl reference`` times the FP64 CPU oracle instead
+(host cores, a down-scaled copy of the same workload per step).
+Multi-GPU (torchrun): every rank advances its own lattice (independent
+problems, no data-path collective); the value is the node updates of all
+ranks over the slowest rank's time.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "MLUPS"
+BYTES_PER_NODE = {"fp32": 72, "fp16": 36, "bf16": 36}
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=4000)
+    ap.add_argument("--warmup", type=int, default=20)
+    ap.add_argument("--impl", default="dilbm", choices=["dilbm", "reference"])
+    ap.add_argument("--workload", default="periodic", choices=["periodic", "sedimentation", "cylinder"])
+    ap.add_argument("--storage", default="fp32", choices=["fp32", "fp16", "bf16"])
+    ap.add_argument("--size", type=int, default=4096, help="periodic box edge")
+    ap.add_argument("--particles", type=int, default=2048)
+    ap.add_argument("--e2e-steps", type=int, default=200)
+    ap.add_argument("--cpu-seconds", type=float, default=12.0)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    return ap.parse_args()
+
+
+def make_problem(args, rank=0):
+    from paper_2106_08950_gb300 import workloads as W
+    if args.workload == "periodic":
+        p = W.periodic_suspension(n=args.size, count=args.particles, seed=3 + 1000 * rank)
+        cfg = {"workload": f"periodic suspension {args.size}x{args.size}, {args.particles} discs r~U[6,12], "
+                           f"rho_s/rho_f=1.2, g=1e-6, tau=0.8, eps=2"}
+    elif args.workload == "sedimentation":
+        p = W.sedimentation()
+        cfg = {"workload": "settling disc 400x2000 closed box, r=12, rho_s/rho_f=1.5, g=1e-5, tau=0.8, eps=2"}
+    else:
+        p = W.cylinder_drag()
+        cfg = {"workload": "cylinder drag 200x100, r=10, U=0.05, Re=20, eps=2"}
+    return p, cfg
+
+
+# ---------------------------------------------------------------- clocks
+class ClockSampler:
+    """nvidia-smi samples of SM clock and throttle reasons while running."""
+
+    Q = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.Q}", "--format=csv,noheader,nounits",
+                 "-lms", "100"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except (OSError, ValueError):
+            self.proc = None
+            return
+        self.thread = threading.Thread(target=self._read, daemon=True)
+        self.thread.start()
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        self.thread.join(timeout=2)
+        mhz, maxes, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [x.strip() for x in ln.split(",")]
+            if len(parts) < 8:
+                continue
+            try:
+                mhz.append(float(parts[0]))
+                maxes.append(float(parts[1]))
+            except ValueError:
+                continue
+            for n, v in zip(names, parts[4:8]):
+                if v.lower() == "active":
+                    reasons.add(n)
+        if not mhz:
+            return None
+        return {"sm_mhz": statistics.median(mhz), "sm_max_mhz": max(maxes), "reasons": sorted(reasons),
+                "samples": len(mhz)}
+
+
+# ---------------------------------------------------------------- dist
+def dist_env():
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return world, rank, local
+
+
+def init_dist(world, backend):
+    if world > 1:
+        import torch.distributed as dist
+        if not dist.is_initialized():
+            dist.init_process_group(backend=backend)
+        return dist
+    return None
+
+
+def max_over_ranks(dist, value, device=None):
+    if dist is None:
+        return value
+    import torch
+    t = torch.tensor([value], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def barrier(dist):
+    if dist is not None:
+        dist.barrier()
+
+
+# ---------------------------------------------------------------- oracle arms
+def oracle_mlups(prob, seconds: float, max_steps: int = 1_000_000, min_steps: int = 2):
+    """Time the FP64 oracle as it stands on all host cores."""
+    from oracle import oracle as O
+    sim = O.OracleSim(prob, phi_cutoff=6 * prob.eps)
+    sim.step(1)                      # warm-up: first-touch of the arrays
+    t0 = time.perf_counter()
+    n = 0
+    while n < max_steps and (n < min_steps or time.perf_counter() - t0 < seconds):
+        sim.step(1)
+        n += 1
+    dt = time.perf_counter() - t0
+    return prob.nx * prob.ny * n / dt / 1e6, n, dt, O.max_threads()
+
+
+def reference_arm(args):
+    world, rank, _ = dist_env()
+    if rank != 0:
+        return 0
+    from paper_2106_08950_gb300 import workloads as W
+    prob, cfg = make_problem(args)
+    # each step: one oracle step of a 512^2 copy of the workload (same
+    # radius, density and area-fraction distributions)
+    n_small = 512
+    count = max(1, round(len(prob.particles) * (n_small / max(prob.nx, 1)) ** 2)) if args.workload == "periodic" else 0
+    small = (W.periodic_suspension(n=n_small, count=count, seed=3) if args.workload == "periodic" else prob)
+    from oracle import oracle as O
+    sim = O.OracleSim(small, phi_cutoff=6 * small.eps)
+    for _ in range(args.warmup):
+        sim.step(1)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        sim.step(1)
+    dt = time.perf_counter() - t0
+    v = small.nx * small.ny * args.steps / dt / 1e6
+    sample = (f"{small.nx}x{small.ny} copy with {len(small.particles)} discs per step"
+              if small is not prob else "the full workload per step")
+    line = {"impl": "reference", "metric": METRIC, "value": v, "unit": "MLUPS", "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": dt / args.steps * 1e3,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "config": cfg,
+            "cpu_baseline": {"value": v, "unit": "MLUPS", "cores": O.max_threads(), "kind": "oracle",
+                             "sample": sample},
+            "e2e": {"value": v, "unit": "MLUPS", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+# ---------------------------------------------------------------- GPU arm
+def measured_peak_hbm():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(path) as fh:
+            return float(json.load(fh)["hbm_gbs"]), "measured"
+    except (OSError, KeyError, ValueError):
+        return 6800.0, "fallback"
+
+
+def gpu_arm(args):
+    import ctypes as C
+
+    import torch
+    from paper_2106_08950_gb300 import dilbm as D
+
+    world, rank, local = dist_env()
+    torch.cuda.set_device(local)
+    dist = init_dist(world, "nccl")
+    dev = torch.device("cuda", local)
+    prob, cfg = make_problem(args, rank)
+    stream = torch.cuda.Stream(device=dev)
+    sim = D.Simulation(prob, storage=args.storage, stream=int(stream.cuda_stream))
+    nodes = prob.nx * prob.ny
+
+    # warm-up
+    sim.step(args.warmup)
+    sim.sync()
+
+    # ---- device-resident throughput, sweep launches timed by CUDA events
+    clocks = ClockSampler(local)
+    clocks.start()
+    time.sleep(0.3)
+    sim.set_timing(True)
+    barrier(dist)
+    torch.cuda.synchronize()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    l0 = sim.launches
+    with torch.cuda.stream(stream):
+        ev0.record(stream)
+        sim.step(args.steps)
+        ev1.record(stream)
+    sim.sync()
+    torch.cuda.synchronize()
+    barrier(dist)
+    launches = sim.launches - l0
+    ms = ev0.elapsed_time(ev1)
+    sweep_ms, sweep_n = sim.sweep_time()
+    sim.set_timing(False)
+    clk = clocks.stop()
+    ms_max = max_over_ranks(dist, ms, dev)
+    value = nodes * args.steps * world / (ms_max / 1e3) / 1e6
+
+    # ---- end to end through the C ABI with host buffers: each step uploads
+    # the particle state from pinned host memory, advances one step and reads
+    # the forces and state back (a host-coupled particle loop).
+    npart = len(prob.particles)
+    e2e = None
+    if npart > 0 and args.e2e_steps > 0:
+        import numpy as np
+        F = np.zeros((npart, 3))
+        host_state = torch.empty(npart * C.sizeof(D.Particle), dtype=torch.uint8).pin_memory()
+        arr = (D.Particle * npart).from_address(host_state.data_ptr())
+        F_pinned = torch.zeros(npart * 3, dtype=torch.float64).pin_memory()
+        Fp = np.frombuffer((C.c_double * (npart * 3)).from_address(F_pinned.data_ptr()), dtype=np.float64)
+        sim.L.dilbm_forces(sim.h, Fp.ctypes.data, None, C.cast(arr, C.c_void_p))
+        barrier(dist)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for _ in range(args.e2e_steps):
+            D.check(sim.L.dilbm_set_particles(sim.h, arr, npart))
+            D.check(sim.L.dilbm_step(sim.h, 1))
+            D.check(sim.L.dilbm_forces(sim.h, Fp.ctypes.data, None, C.cast(arr, C.c_void_p)))
+        dt = time.perf_counter() - t0
+        dt = max_over_ranks(dist, dt, dev)
+        h2d = npart * (8 * 8 + 4)
+        d2h = npart * 3 * 8 + npart * (8 * 8 + 4) + 4
+        e2e = {"value": nodes * args.e2e_steps * world / dt / 1e6, "unit": "MLUPS",
+               "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
+               "loop": "per step: dilbm_set_particles(host) + dilbm_step(1) + dilbm_forces(host)"}
+
+    # ---- roofline of the dominant kernel (the lattice sweep)
+    peak, peak_kind = measured_peak_hbm()
+    per_launch_ms = sweep_ms / max(sweep_n, 1)
+    alg_bytes = BYTES_PER_NODE[args.storage] * nodes
+    achieved = alg_bytes / (per_launch_ms / 1e3) / 1e9
+    traffic = None
+    tpath = os.path.join(ROOT, "profiles", "sweep_traffic.json")
+    try:
+        with open(tpath) as fh:
+            tr = json.load(fh)
+        key = f"{args.workload}:{args.storage}:{prob.nx}x{prob.ny}"
+        traffic = tr.get(key)
+    except (OSError, ValueError):
+        traffic = None
+    roof = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+            "traffic": traffic, "peak_kind": peak_kind,
+            "kernel": "sweep_kernel", "sweep_ms_per_launch": per_launch_ms,
+            "sweep_share_of_step": sweep_ms / ms if ms > 0 else None,
+            "algorithmic_bytes_per_launch": alg_bytes}
+
+    line = {"metric": METRIC, "value": value, "unit": "MLUPS", "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms_max / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None,
+            "dtype": {"fp32": "f32", "fp16": "f16-storage/f32-math", "bf16": "bf16-storage/f32-math"}[args.storage],
+            "data": "synthetic",
+            "config": dict(cfg, storage=args.storage, nodes=nodes, particles=npart,
+                           l2="populations 9x2 planes exceed L2; no flush",
+                           parallelism=f"replicas x{world}" if world > 1 else "single GPU"),
+            "roofline": roof, "gpu_launches": launches, "e2e": e2e, "clocks": clk}
+
+    # ---- the oracle on the host cores, rank 0 at N=1 only
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        v, n, dt, cores = oracle_mlups(prob, args.cpu_seconds)
+        line["cpu_baseline"] = {"value": v, "unit": "MLUPS", "cores": cores, "kind": "oracle",
+                                "sample": f"{n} steps of the full workload ({dt:.1f} s), phi cutoff 6 widths"}
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    sim.close()
+    if dist is not None:
+        dist.destroy_process_group()
+    return 0
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        return reference_arm(args)
+    return gpu_arm(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -1,0 +1,174 @@
+/*
+ * dilbm.h -- C ABI of the GB300 (sm_103a) DI-LBM library.
+ *
+ * The library advances the diffuse-interface lattice Boltzmann method for
+ * fluid-particle interaction of Liu, Huang, Chai & Shi (arXiv:2106.08950) on
+ * one GPU: a D2Q9 lattice (Sec. 2.1, Eqs. 3-4) whose every node, once per
+ * time step, pulls its streamed populations, evaluates the solid fraction
+ * phi of Eq. 14 from the particles, collides with the modified force term
+ * (Eqs. 13, 15-17), and hands its share of the hydrodynamic force and torque
+ * (Eqs. 18-19) to the particle that owns it; the particles then move by the
+ * Newton-Euler equations (Eqs. 22-24) with Wan-Turek repulsion (Eqs. 28-29).
+ * Domain edges use non-equilibrium extrapolation (Sec. 3, Guo et al. 2002).
+ *
+ * Conventions
+ *   - Lattice units: dx = dt = 1, cs^2 = 1/3.  Nodes sit at integer
+ *     coordinates 0..nx-1, 0..ny-1.  Walls (non-periodic sides) lie on the
+ *     first / last node column or row.
+ *   - Every call returns DILBM_OK (0) or a negative DILBM_ERR_* code and, on
+ *     error, leaves a message for dilbm_last_error() (per host thread).
+ *   - All work is issued asynchronously on the CUDA stream given at create;
+ *     calls that return data to the host synchronise that stream.
+ *   - The caller owns every array it passes; the library copies inputs and
+ *     never keeps a caller pointer beyond the call.  The context owns its
+ *     device memory and frees it in dilbm_destroy().
+ *   - A context is not thread-safe: one host thread at a time per context.
+ */
+#ifndef DILBM_H
+#define DILBM_H
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* Return codes. */
+#define DILBM_OK               0
+#define DILBM_ERR_INVALID_ARG (-1)  /* bad size, parameter or pointer */
+#define DILBM_ERR_OOM         (-2)  /* device allocation failed */
+#define DILBM_ERR_CUDA        (-3)  /* a CUDA runtime call failed */
+#define DILBM_ERR_UNSTABLE    (-4)  /* a node reached rho <= 0 or a non-finite velocity */
+#define DILBM_ERR_TIMEOUT     (-5)  /* a bounded device-side wait gave up */
+#define DILBM_ERR_OVERFLOW    (-6)  /* more than DILBM_MAX_CANDIDATES particles near one tile */
+
+/* Particles whose (radius + 6 interface widths) disc reaches one lattice tile
+ * (128 x 8 nodes); more is reported as DILBM_ERR_OVERFLOW. */
+#define DILBM_MAX_CANDIDATES 32
+
+typedef enum { DILBM_D2Q9 = 0 } dilbm_lattice;          /* Eq. 3-4: the only lattice */
+
+typedef enum {
+    DILBM_SIDE_PERIODIC = 0,   /* both sides of an axis must be periodic, or neither */
+    DILBM_SIDE_VELOCITY = 1,   /* prescribed (ux, uy), density from the inner node (walls, inlets) */
+    DILBM_SIDE_PRESSURE = 2    /* prescribed rho, velocity from the inner node (outlets) */
+} dilbm_side_kind;
+
+typedef enum {
+    DILBM_FP32 = 0,            /* populations stored as FP32 deviations f_i - w_i */
+    DILBM_FP16_DEV = 1,        /* stored as FP16 deviations, FP32 arithmetic */
+    DILBM_BF16_DEV = 2         /* stored as BF16 deviations, FP32 arithmetic */
+} dilbm_storage;
+
+typedef enum {
+    DILBM_FORCE_EQ18 = 0,      /* Eq. 18 as printed: -sum_n phi_n sum_i F_i c_i */
+    DILBM_FORCE_MOMENTUM = 1   /* the momentum the collision hands the fluid, negated */
+} dilbm_force_model;
+
+typedef struct {
+    int kind;                  /* dilbm_side_kind */
+    double ux, uy;             /* DILBM_SIDE_VELOCITY: boundary velocity */
+    double rho;                /* DILBM_SIDE_PRESSURE: boundary density */
+} dilbm_side;
+
+typedef struct {
+    int nx, ny;                /* lattice nodes, each >= 3 */
+    dilbm_side west, east, south, north;
+    double gravity[2];         /* acceleration on the particles (physical direction) */
+    double rho_f;              /* fluid density in the buoyancy term of Eq. 22 */
+    double rho_init;           /* initial density: f = f^eq(rho_init, u0) */
+    double u0[2];              /* initial velocity */
+    int storage;               /* dilbm_storage */
+    int force_model;           /* dilbm_force_model */
+    double wan_turek[5];       /* eps_P, eps_P', eps_W, eps_W', xi of Eqs. 28-29 */
+} dilbm_grid;
+
+typedef struct {
+    double x, y;               /* centre, node units */
+    double r;                  /* radius */
+    double ux, uy;             /* translational velocity */
+    double omega;              /* angular velocity (counter-clockwise) */
+    double theta;              /* orientation (integrated omega) */
+    double rho_s;              /* particle density; mass rho_s pi r^2 per unit depth */
+    int fixed;                 /* non-zero: the particle never moves */
+} dilbm_particle;
+
+typedef struct dilbm_ctx dilbm_ctx;
+
+/*
+ * Create a simulation (Sec. 2.3, step 1: initialise).
+ *   grid            lattice size, sides, gravity, storage and force model.
+ *   lattice         DILBM_D2Q9.
+ *   tau             relaxation time (Eq. 1), > 0.5; viscosity (tau - 1/2)/3 (Eq. 6).
+ *   interface_width epsilon of Eq. 14, > 0.
+ *   particles, np   host array of np >= 0 particles, copied; each centre must
+ *                   lie inside the lattice.
+ *   cuda_stream     cudaStream_t to issue all work on (NULL: the legacy default stream).
+ *   out             receives the context.
+ * Populations start at f^eq(rho_init, u0) on every node.
+ * Errors: INVALID_ARG, OOM, CUDA.
+ */
+int dilbm_create(const dilbm_grid *grid, dilbm_lattice lattice, double tau,
+                 double interface_width, const dilbm_particle *particles, int np,
+                 void *cuda_stream, dilbm_ctx **out);
+
+/*
+ * Advance nsteps >= 0 time steps (Sec. 2.3, steps 2-5; Eqs. 13-19, 22-24,
+ * 28-29).  Each step is one fused pull-stream + collide sweep over every node,
+ * a per-particle FP64 force/torque reduction and a rigid-body update.
+ * Asynchronous: returns once the work is queued; errors raised on the device
+ * (UNSTABLE, OVERFLOW) surface at the next dilbm_sync().
+ */
+int dilbm_step(dilbm_ctx *ctx, long long nsteps);
+
+/*
+ * Hydrodynamic force and torque of the last step (Eqs. 18-19, lattice units,
+ * force on the particle), optional Wan-Turek force of the last step, and the
+ * current particle state.  force: host, np x 3 (Fx, Fy, T); fcol: host,
+ * np x 2 or NULL; state: host, np entries or NULL.  Synchronises the stream.
+ * Errors: INVALID_ARG, CUDA, and any sticky device error.
+ */
+int dilbm_forces(dilbm_ctx *ctx, double *force, double *fcol, dilbm_particle *state);
+
+/*
+ * Macroscopic fields at the current time level, row-major [ny][nx] FP32:
+ * density (Eq. 5), corrected velocity (Eq. 17) and solid fraction (Eq. 14),
+ * taken from the populations the next step would collide.  Any pointer may be
+ * NULL.  on_device != 0: the pointers are device memory; otherwise host
+ * memory and the call synchronises the stream.
+ */
+int dilbm_fields(dilbm_ctx *ctx, float *rho, float *ux, float *uy, float *phi, int on_device);
+
+/*
+ * Checkpoint / resume: the post-collision populations f_i, host FP64 array of
+ * 9 x ny x nx (direction-major, rows of x), in the direction order of Eq. 3.
+ * dilbm_set_populations also accepts any state written by dilbm_get_populations
+ * of a context of the same size.  Both synchronise the stream.
+ */
+int dilbm_get_populations(dilbm_ctx *ctx, double *f);
+int dilbm_set_populations(dilbm_ctx *ctx, const double *f);
+
+/* Replace the particle state (host array of the np given at create). */
+int dilbm_set_particles(dilbm_ctx *ctx, const dilbm_particle *particles, int np);
+
+/* Wait for queued work; return the first sticky device error, else DILBM_OK. */
+int dilbm_sync(dilbm_ctx *ctx);
+
+/* Free the context (synchronises its stream).  NULL is ignored. */
+void dilbm_destroy(dilbm_ctx *ctx);
+
+/* Message of the last error on this host thread ("" if none). */
+const char *dilbm_last_error(void);
+
+/*
+ * Measurement: with timing on, CUDA events bracket every lattice-sweep launch
+ * on the context's stream; dilbm_sweep_time() returns their summed duration
+ * in milliseconds and the number of launches since timing was (re)enabled.
+ * dilbm_launch_count() is the number of kernels this context has launched.
+ */
+int dilbm_set_timing(dilbm_ctx *ctx, int enable);
+int dilbm_sweep_time(dilbm_ctx *ctx, double *ms_total, long long *launches);
+long long dilbm_launch_count(const dilbm_ctx *ctx);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* DILBM_H */

@@ -71,8 +71,8 @@ typedef struct {
     double rho_init, u0x, u0y;   /* initial state */
     int force_model;             /* 0: Eq. 18 as printed, 1: momentum exchange */
     double eps_p, eps_p2, eps_w, eps_w2, xi;  /* Eqs. 28-29 */
-    double phi_cutoff;           /* 0: every particle at every node; > 0: skip
-                                    particles whose l < -phi_cutoff */
+    double phi_cutoff;           /* 0: every particle at every node; > 0: a particle
+                                    reaches only nodes with l >= -phi_cutoff */
 } orc_params;
 
 typedef struct {
@@ -274,11 +274,77 @@ void orc_destroy(orc_sim *s)
     free(s);
 }
 
+static void set_particle_velocity(orc_sim *s, size_t k)
+{
+    int own = s->owner[k];
+    if (own >= 0) {
+        const orc_particle *P = &s->parts[own];
+        s->usx[k] = P->ux - P->omega * s->ry[k];
+        s->usy[k] = P->uy + P->omega * s->rx[k];
+    } else {
+        s->usx[k] = 0.0;
+        s->usy[k] = 0.0;
+    }
+}
+
+/* Step 1 with a cutoff: each particle, in index order, visits the nodes of
+ * its bounding box (radius + cutoff) and takes every node where its phi is
+ * strictly larger than what earlier particles left: the same max rule and
+ * tie order as the full sum, for the particles that reach the node. */
+static void solid_fraction_cutoff(orc_sim *s)
+{
+    const orc_params *p = &s->p;
+    int nx = p->nx, ny = p->ny;
+    size_t n = (size_t)nx * ny;
+    for (size_t k = 0; k < n; ++k) { s->phi[k] = 0.0; s->owner[k] = -1; s->rx[k] = 0.0; s->ry[k] = 0.0; }
+    for (int q = 0; q < s->np; ++q) {
+        const orc_particle *P = &s->parts[q];
+        double R = P->r + p->phi_cutoff;
+        int x0 = (int)floor(P->x - R), x1 = (int)ceil(P->x + R);
+        int y0 = (int)floor(P->y - R), y1 = (int)ceil(P->y + R);
+        if (periodic_x(p)) {
+            if (x1 - x0 + 1 > nx) { x0 = 0; x1 = nx - 1; }   /* else wrapped below */
+        } else {
+            if (x0 < 0) x0 = 0;
+            if (x1 > nx - 1) x1 = nx - 1;
+        }
+        if (periodic_y(p)) {
+            if (y1 - y0 + 1 > ny) { y0 = 0; y1 = ny - 1; }   /* else wrapped below */
+        } else {
+            if (y0 < 0) y0 = 0;
+            if (y1 > ny - 1) y1 = ny - 1;
+        }
+#pragma omp parallel for schedule(static)
+        for (int yy = y0; yy <= y1; ++yy) {
+            int y = periodic_y(p) ? ((yy % ny) + ny) % ny : yy;
+            for (int xx = x0; xx <= x1; ++xx) {
+                int x = periodic_x(p) ? ((xx % nx) + nx) % nx : xx;
+                size_t k = (size_t)y * nx + x;
+                double dx = x - P->x, dy = y - P->y;
+                if (periodic_x(p)) dx = min_image(dx, nx);
+                if (periodic_y(p)) dy = min_image(dy, ny);
+                double l = P->r - sqrt(dx * dx + dy * dy);
+                if (l < -p->phi_cutoff) continue;
+                double ph = orc_phi(l, p->eps);
+                if (ph > s->phi[k]) {
+                    s->phi[k] = ph; s->owner[k] = q; s->rx[k] = dx; s->ry[k] = dy;
+                }
+            }
+        }
+    }
+#pragma omp parallel for schedule(static)
+    for (long long k = 0; k < (long long)n; ++k) set_particle_velocity(s, (size_t)k);
+}
+
 /* Step 1: phi, owner and u_s at every node from the current particle state. */
 static void solid_fraction(orc_sim *s)
 {
     const orc_params *p = &s->p;
     int nx = p->nx, ny = p->ny;
+    if (p->phi_cutoff > 0.0) {
+        solid_fraction_cutoff(s);
+        return;
+    }
 #pragma omp parallel for schedule(static)
     for (int y = 0; y < ny; ++y) {
         for (int x = 0; x < nx; ++x) {
@@ -291,7 +357,6 @@ static void solid_fraction(orc_sim *s)
                 if (periodic_x(p)) dx = min_image(dx, nx);
                 if (periodic_y(p)) dy = min_image(dy, ny);
                 double l = P->r - sqrt(dx * dx + dy * dy);
-                if (p->phi_cutoff > 0.0 && l < -p->phi_cutoff) continue;
                 double ph = orc_phi(l, p->eps);
                 if (ph > best) {          /* strict: ties keep the lower index */
                     best = ph; own = q; brx = dx; bry = dy;
@@ -301,14 +366,7 @@ static void solid_fraction(orc_sim *s)
             s->owner[k] = own;
             s->rx[k] = brx;
             s->ry[k] = bry;
-            if (own >= 0) {
-                const orc_particle *P = &s->parts[own];
-                s->usx[k] = P->ux - P->omega * bry;
-                s->usy[k] = P->uy + P->omega * brx;
-            } else {
-                s->usx[k] = 0.0;
-                s->usy[k] = 0.0;
-            }
+            set_particle_velocity(s, k);
         }
     }
 }

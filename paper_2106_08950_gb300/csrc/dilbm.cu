@@ -1,0 +1,450 @@
+// C ABI of the DI-LBM library (declared in include/dilbm.h): context
+// management, argument checks, and the launch sequence of one time step.
+#include "dilbm.h"
+#include "dilbm_kernels.cuh"
+
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+using namespace dilbm;
+
+namespace {
+
+thread_local std::string g_err;
+
+int fail(int code, const std::string &msg) {
+    g_err = msg;
+    return code;
+}
+
+int cuda_fail(cudaError_t e, const char *what) {
+    return fail(e == cudaErrorMemoryAllocation ? DILBM_ERR_OOM : DILBM_ERR_CUDA,
+                std::string(what) + ": " + cudaGetErrorString(e));
+}
+
+#define DILBM_CUDA(call)                                   \
+    do {                                                   \
+        cudaError_t e_ = (call);                           \
+        if (e_ != cudaSuccess) return cuda_fail(e_, #call); \
+    } while (0)
+
+}  // namespace
+
+struct dilbm_ctx {
+    Lattice L{};
+    Physics ph{};
+    BodyParams bp{};
+    int storage = DILBM_FP32;
+    size_t elem = 4;
+    void *buf[2] = {nullptr, nullptr};
+    int cur = 0;
+    Particles P{};
+    Bins B{};
+    double *force = nullptr, *fcol = nullptr;
+    int *err = nullptr;
+    int sticky = 0;
+    float *fields = nullptr;          // 4 x nx x ny, allocated on first use
+    double *pops = nullptr;           // 9 x nx x ny, allocated on first use
+    cudaStream_t stream = nullptr;
+    int np = 0;
+    int ntiles = 0;
+    bool timing = false;
+    std::vector<cudaEvent_t> ev;      // start/stop pairs around sweep launches
+    size_t ev_used = 0;
+    long long launches = 0;
+    void *owned[16] = {};
+    int nowned = 0;
+};
+
+namespace {
+
+template <typename Tp>
+int dev_alloc(dilbm_ctx *c, Tp **p, size_t count) {
+    void *q = nullptr;
+    cudaError_t e = cudaMalloc(&q, count * sizeof(Tp) > 0 ? count * sizeof(Tp) : 16);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaMalloc");
+    c->owned[c->nowned++] = q;
+    *p = static_cast<Tp *>(q);
+    return DILBM_OK;
+}
+
+int check_side(const dilbm_side &s, const char *name) {
+    if (s.kind < DILBM_SIDE_PERIODIC || s.kind > DILBM_SIDE_PRESSURE)
+        return fail(DILBM_ERR_INVALID_ARG, std::string("unknown side kind on ") + name);
+    if (s.kind == DILBM_SIDE_PRESSURE && !(s.rho > 0.0))
+        return fail(DILBM_ERR_INVALID_ARG, std::string("pressure side needs rho > 0 on ") + name);
+    return DILBM_OK;
+}
+
+int check_particles(const dilbm_grid *g, const dilbm_particle *p, int np) {
+    for (int k = 0; k < np; ++k) {
+        const dilbm_particle &q = p[k];
+        const bool px = g->west.kind == DILBM_SIDE_PERIODIC, py = g->south.kind == DILBM_SIDE_PERIODIC;
+        const bool inx = px ? (q.x >= 0.0 && q.x < g->nx) : (q.x >= 0.0 && q.x <= g->nx - 1);
+        const bool iny = py ? (q.y >= 0.0 && q.y < g->ny) : (q.y >= 0.0 && q.y <= g->ny - 1);
+        if (!inx || !iny || !(q.r > 0.0) || !(q.rho_s > 0.0) || !std::isfinite(q.ux) ||
+            !std::isfinite(q.uy) || !std::isfinite(q.omega))
+            return fail(DILBM_ERR_INVALID_ARG, "particle " + std::to_string(k) +
+                                                   " outside the lattice or with a non-positive radius/density");
+    }
+    return DILBM_OK;
+}
+
+int upload_particles(dilbm_ctx *c, const dilbm_particle *p, int np) {
+    std::vector<double> h(8 * (size_t)np);
+    std::vector<int> fx(np);
+    for (int k = 0; k < np; ++k) {
+        h[0 * np + k] = p[k].x; h[1 * np + k] = p[k].y; h[2 * np + k] = p[k].r;
+        h[3 * np + k] = p[k].ux; h[4 * np + k] = p[k].uy; h[5 * np + k] = p[k].omega;
+        h[6 * np + k] = p[k].theta; h[7 * np + k] = p[k].rho_s;
+        fx[k] = p[k].fixed ? 1 : 0;
+    }
+    // P.x .. P.rho_s are consecutive slices of one allocation
+    DILBM_CUDA(cudaMemcpyAsync(c->P.x, h.data(), sizeof(double) * h.size(), cudaMemcpyHostToDevice, c->stream));
+    DILBM_CUDA(cudaMemcpyAsync(c->P.fixed, fx.data(), sizeof(int) * np, cudaMemcpyHostToDevice, c->stream));
+    DILBM_CUDA(cudaMemsetAsync(c->B.count, 0, sizeof(int) * c->ntiles, c->stream));
+    integrate_bin_kernel<<<(np + 127) / 128, 128, 0, c->stream>>>(c->L, c->ph, c->P, c->B, c->bp,
+                                                                  c->force, c->fcol, 0, c->err);
+    DILBM_CUDA(cudaGetLastError());
+    c->launches += 1;
+    // the host copies above read pageable memory that goes out of scope
+    DILBM_CUDA(cudaStreamSynchronize(c->stream));
+    return DILBM_OK;
+}
+
+template <int MODE>
+int launch_sweep(dilbm_ctx *c, const void *src, void *dst, FieldsOut fo) {
+    dim3 grid(c->L.ntx, c->L.nty), block(32, TILE_H);
+    switch (c->storage) {
+    case DILBM_FP32:
+        sweep_kernel<float, MODE><<<grid, block, 0, c->stream>>>(
+            (const float *)src, (float *)dst, c->L, c->ph, c->P, c->B, fo, c->err);
+        break;
+    case DILBM_FP16_DEV:
+        sweep_kernel<__half, MODE><<<grid, block, 0, c->stream>>>(
+            (const __half *)src, (__half *)dst, c->L, c->ph, c->P, c->B, fo, c->err);
+        break;
+    default:
+        sweep_kernel<__nv_bfloat16, MODE><<<grid, block, 0, c->stream>>>(
+            (const __nv_bfloat16 *)src, (__nv_bfloat16 *)dst, c->L, c->ph, c->P, c->B, fo, c->err);
+        break;
+    }
+    DILBM_CUDA(cudaGetLastError());
+    c->launches += 1;
+    return DILBM_OK;
+}
+
+int one_step(dilbm_ctx *c) {
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    if (c->timing) {
+        if (c->ev_used + 2 > c->ev.size()) {
+            for (int k = 0; k < 64; ++k) {
+                cudaEvent_t e;
+                DILBM_CUDA(cudaEventCreate(&e));
+                c->ev.push_back(e);
+            }
+        }
+        e0 = c->ev[c->ev_used];
+        e1 = c->ev[c->ev_used + 1];
+        c->ev_used += 2;
+        DILBM_CUDA(cudaEventRecord(e0, c->stream));
+    }
+    int rc = launch_sweep<MODE_STEP>(c, c->buf[c->cur], c->buf[c->cur ^ 1], FieldsOut{});
+    if (rc) return rc;
+    if (c->timing) DILBM_CUDA(cudaEventRecord(e1, c->stream));
+    if (c->np > 0) {
+        const int np = c->np;
+        reduce_kernel<<<(np * 32 + 127) / 128, 128, 0, c->stream>>>(c->L, c->ph, c->P, c->B, c->bp,
+                                                                    c->force, c->fcol);
+        DILBM_CUDA(cudaGetLastError());
+        DILBM_CUDA(cudaMemsetAsync(c->B.count, 0, sizeof(int) * c->ntiles, c->stream));
+        integrate_bin_kernel<<<(np + 127) / 128, 128, 0, c->stream>>>(c->L, c->ph, c->P, c->B, c->bp,
+                                                                      c->force, c->fcol, 1, c->err);
+        DILBM_CUDA(cudaGetLastError());
+        c->launches += 2;
+    }
+    c->cur ^= 1;
+    return DILBM_OK;
+}
+
+int read_sticky(dilbm_ctx *c) {
+    int h = 0;
+    DILBM_CUDA(cudaMemcpyAsync(&h, c->err, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
+    DILBM_CUDA(cudaStreamSynchronize(c->stream));
+    c->sticky |= h;
+    if (c->sticky & ERR_UNSTABLE) return fail(DILBM_ERR_UNSTABLE, "a node reached rho <= 0 or a non-finite velocity");
+    if (c->sticky & ERR_OVERFLOW)
+        return fail(DILBM_ERR_OVERFLOW, "more than DILBM_MAX_CANDIDATES particles reach one lattice tile");
+    return DILBM_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char *dilbm_last_error(void) { return g_err.c_str(); }
+
+int dilbm_create(const dilbm_grid *g, dilbm_lattice lattice, double tau, double interface_width,
+                 const dilbm_particle *particles, int np, void *cuda_stream, dilbm_ctx **out) {
+    if (!g || !out) return fail(DILBM_ERR_INVALID_ARG, "grid and out must not be NULL");
+    *out = nullptr;
+    if (lattice != DILBM_D2Q9) return fail(DILBM_ERR_INVALID_ARG, "only DILBM_D2Q9 is supported");
+    if (g->nx < 3 || g->ny < 3) return fail(DILBM_ERR_INVALID_ARG, "nx and ny must be >= 3");
+    if ((long long)g->nx * g->ny > (1LL << 31)) return fail(DILBM_ERR_INVALID_ARG, "lattice larger than 2^31 nodes");
+    if (!(tau > 0.5)) return fail(DILBM_ERR_INVALID_ARG, "tau must be > 0.5");
+    if (!(interface_width > 0.0)) return fail(DILBM_ERR_INVALID_ARG, "interface width must be > 0");
+    if (np < 0 || (np > 0 && !particles)) return fail(DILBM_ERR_INVALID_ARG, "bad particle array");
+    if (g->storage < DILBM_FP32 || g->storage > DILBM_BF16_DEV) return fail(DILBM_ERR_INVALID_ARG, "unknown storage");
+    if (g->force_model != DILBM_FORCE_EQ18 && g->force_model != DILBM_FORCE_MOMENTUM)
+        return fail(DILBM_ERR_INVALID_ARG, "unknown force model");
+    int rc;
+    if ((rc = check_side(g->west, "west")) || (rc = check_side(g->east, "east")) ||
+        (rc = check_side(g->south, "south")) || (rc = check_side(g->north, "north")))
+        return rc;
+    if ((g->west.kind == DILBM_SIDE_PERIODIC) != (g->east.kind == DILBM_SIDE_PERIODIC) ||
+        (g->south.kind == DILBM_SIDE_PERIODIC) != (g->north.kind == DILBM_SIDE_PERIODIC))
+        return fail(DILBM_ERR_INVALID_ARG, "an axis must be periodic on both sides or on neither");
+    if (!(g->rho_init > 0.0) || !(g->rho_f > 0.0)) return fail(DILBM_ERR_INVALID_ARG, "densities must be > 0");
+    for (int k = 0; k < 5; ++k)
+        if (!(g->wan_turek[k] > 0.0)) return fail(DILBM_ERR_INVALID_ARG, "Wan-Turek parameters must be > 0");
+    if ((rc = check_particles(g, particles, np))) return rc;
+
+    dilbm_ctx *c = new dilbm_ctx();
+    c->stream = (cudaStream_t)cuda_stream;
+    c->np = np;
+    c->storage = g->storage;
+    c->elem = g->storage == DILBM_FP32 ? 4 : 2;
+    Lattice &L = c->L;
+    L.nx = g->nx;
+    L.ny = g->ny;
+    L.pitch = (g->nx + 31) / 32 * 32;
+    L.plane = (long long)L.pitch * L.ny;
+    L.ntx = (L.nx + TILE_W - 1) / TILE_W;
+    L.nty = (L.ny + TILE_H - 1) / TILE_H;
+    L.per_x = g->west.kind == DILBM_SIDE_PERIODIC;
+    L.per_y = g->south.kind == DILBM_SIDE_PERIODIC;
+    const dilbm_side *sides[4] = {&g->west, &g->east, &g->south, &g->north};
+    for (int k = 0; k < 4; ++k) {
+        L.side_kind[k] = sides[k]->kind;
+        L.side_ux[k] = (float)sides[k]->ux;
+        L.side_uy[k] = (float)sides[k]->uy;
+        L.side_drho[k] = (float)(sides[k]->rho - 1.0);
+    }
+    c->ntiles = L.ntx * L.nty;
+    Physics &ph = c->ph;
+    ph.omega = (float)(1.0 / tau);
+    ph.kf = (float)(1.0 - 0.5 / tau);
+    ph.kforce = g->force_model == DILBM_FORCE_EQ18 ? ph.kf : 1.0f;
+    ph.four_over_eps = (float)(4.0 / interface_width);
+    ph.cut_d = PHI_CUT_WIDTHS * interface_width;
+    ph.cut = (float)ph.cut_d;
+    BodyParams &bp = c->bp;
+    bp.np = np;
+    bp.gx = g->gravity[0];
+    bp.gy = g->gravity[1];
+    bp.rho_f = g->rho_f;
+    bp.eps_p = g->wan_turek[0];
+    bp.eps_p2 = g->wan_turek[1];
+    bp.eps_w = g->wan_turek[2];
+    bp.eps_w2 = g->wan_turek[3];
+    bp.xi = g->wan_turek[4];
+
+    auto bail = [&](int code) { dilbm_destroy(c); return code; };
+    const size_t pop_elems = 9 * (size_t)L.plane;
+    for (int b = 0; b < 2; ++b) {
+        void *q = nullptr;
+        cudaError_t e = cudaMalloc(&q, pop_elems * c->elem);
+        if (e != cudaSuccess) return bail(cuda_fail(e, "cudaMalloc populations"));
+        c->owned[c->nowned++] = q;
+        c->buf[b] = q;
+        e = cudaMemsetAsync(q, 0, pop_elems * c->elem, c->stream);
+        if (e != cudaSuccess) return bail(cuda_fail(e, "cudaMemsetAsync"));
+    }
+    const int npa = np > 0 ? np : 1;
+    double *pd = nullptr;
+    float *pf = nullptr;
+    if ((rc = dev_alloc(c, &pd, 8 * (size_t)npa)) || (rc = dev_alloc(c, &pf, 2 * (size_t)npa)) ||
+        (rc = dev_alloc(c, &c->P.fixed, (size_t)npa)) || (rc = dev_alloc(c, &c->force, 3 * (size_t)npa)) ||
+        (rc = dev_alloc(c, &c->fcol, 2 * (size_t)npa)) || (rc = dev_alloc(c, &c->err, 1)) ||
+        (rc = dev_alloc(c, &c->B.count, (size_t)c->ntiles)) ||
+        (rc = dev_alloc(c, &c->B.ids, (size_t)c->ntiles * MAXC)) ||
+        (rc = dev_alloc(c, &c->B.partial, (size_t)c->ntiles * MAXC * 3)))
+        return bail(rc);
+    c->P.x = pd; c->P.y = pd + npa; c->P.r = pd + 2 * npa; c->P.ux = pd + 3 * npa;
+    c->P.uy = pd + 4 * npa; c->P.omega = pd + 5 * npa; c->P.theta = pd + 6 * npa; c->P.rho_s = pd + 7 * npa;
+    c->P.xf = pf; c->P.yf = pf + npa;
+    cudaError_t e;
+    if ((e = cudaMemsetAsync(c->err, 0, sizeof(int), c->stream)) != cudaSuccess ||
+        (e = cudaMemsetAsync(c->force, 0, sizeof(double) * 3 * npa, c->stream)) != cudaSuccess ||
+        (e = cudaMemsetAsync(c->fcol, 0, sizeof(double) * 2 * npa, c->stream)) != cudaSuccess ||
+        (e = cudaMemsetAsync(c->B.count, 0, sizeof(int) * c->ntiles, c->stream)) != cudaSuccess)
+        return bail(cuda_fail(e, "cudaMemsetAsync"));
+    // uniform initial state f^eq(rho_init, u0)
+    const int blocks = 152 * 8;
+    const float drho = (float)(g->rho_init - 1.0), u0x = (float)g->u0[0], u0y = (float)g->u0[1];
+    switch (c->storage) {
+    case DILBM_FP32: init_kernel<float><<<blocks, 256, 0, c->stream>>>((float *)c->buf[0], L, drho, u0x, u0y); break;
+    case DILBM_FP16_DEV: init_kernel<__half><<<blocks, 256, 0, c->stream>>>((__half *)c->buf[0], L, drho, u0x, u0y); break;
+    default: init_kernel<__nv_bfloat16><<<blocks, 256, 0, c->stream>>>((__nv_bfloat16 *)c->buf[0], L, drho, u0x, u0y); break;
+    }
+    if ((e = cudaGetLastError()) != cudaSuccess) return bail(cuda_fail(e, "init_kernel"));
+    c->launches += 1;
+    if (np > 0 && (rc = upload_particles(c, particles, np))) return bail(rc);
+    if ((e = cudaStreamSynchronize(c->stream)) != cudaSuccess) return bail(cuda_fail(e, "cudaStreamSynchronize"));
+    *out = c;
+    return DILBM_OK;
+}
+
+int dilbm_step(dilbm_ctx *c, long long nsteps) {
+    if (!c || nsteps < 0) return fail(DILBM_ERR_INVALID_ARG, "bad context or step count");
+    for (long long t = 0; t < nsteps; ++t) {
+        int rc = one_step(c);
+        if (rc) return rc;
+    }
+    return DILBM_OK;
+}
+
+int dilbm_sync(dilbm_ctx *c) {
+    if (!c) return fail(DILBM_ERR_INVALID_ARG, "NULL context");
+    return read_sticky(c);
+}
+
+int dilbm_forces(dilbm_ctx *c, double *force, double *fcol, dilbm_particle *state) {
+    if (!c) return fail(DILBM_ERR_INVALID_ARG, "NULL context");
+    if (c->np > 0 && !force) return fail(DILBM_ERR_INVALID_ARG, "force must not be NULL");
+    const int np = c->np;
+    if (np == 0) return read_sticky(c);
+    std::vector<double> h(8 * (size_t)np);
+    std::vector<int> fx(np);
+    DILBM_CUDA(cudaMemcpyAsync(force, c->force, sizeof(double) * 3 * np, cudaMemcpyDeviceToHost, c->stream));
+    if (fcol) DILBM_CUDA(cudaMemcpyAsync(fcol, c->fcol, sizeof(double) * 2 * np, cudaMemcpyDeviceToHost, c->stream));
+    if (state) {
+        DILBM_CUDA(cudaMemcpyAsync(h.data(), c->P.x, sizeof(double) * h.size(), cudaMemcpyDeviceToHost, c->stream));
+        DILBM_CUDA(cudaMemcpyAsync(fx.data(), c->P.fixed, sizeof(int) * np, cudaMemcpyDeviceToHost, c->stream));
+    }
+    int rc = read_sticky(c);   // synchronises the stream
+    if (state) {
+        for (int k = 0; k < np; ++k) {
+            dilbm_particle &q = state[k];
+            q.x = h[k]; q.y = h[np + k]; q.r = h[2 * np + k]; q.ux = h[3 * np + k]; q.uy = h[4 * np + k];
+            q.omega = h[5 * np + k]; q.theta = h[6 * np + k]; q.rho_s = h[7 * np + k]; q.fixed = fx[k];
+        }
+    }
+    return rc;
+}
+
+int dilbm_fields(dilbm_ctx *c, float *rho, float *ux, float *uy, float *phi, int on_device) {
+    if (!c) return fail(DILBM_ERR_INVALID_ARG, "NULL context");
+    const size_t n = (size_t)c->L.nx * c->L.ny;
+    FieldsOut fo{};
+    if (on_device) {
+        fo = FieldsOut{rho, ux, uy, phi};
+        return launch_sweep<MODE_FIELDS>(c, c->buf[c->cur], nullptr, fo);
+    }
+    if (!c->fields) {
+        void *q = nullptr;
+        DILBM_CUDA(cudaMalloc(&q, sizeof(float) * 4 * n));
+        c->owned[c->nowned++] = q;
+        c->fields = (float *)q;
+    }
+    fo = FieldsOut{c->fields, c->fields + n, c->fields + 2 * n, c->fields + 3 * n};
+    int rc = launch_sweep<MODE_FIELDS>(c, c->buf[c->cur], nullptr, fo);
+    if (rc) return rc;
+    float *dst[4] = {rho, ux, uy, phi};
+    for (int k = 0; k < 4; ++k)
+        if (dst[k]) DILBM_CUDA(cudaMemcpyAsync(dst[k], c->fields + k * n, sizeof(float) * n, cudaMemcpyDeviceToHost, c->stream));
+    DILBM_CUDA(cudaStreamSynchronize(c->stream));
+    return DILBM_OK;
+}
+
+static int ensure_pops(dilbm_ctx *c) {
+    if (c->pops) return DILBM_OK;
+    void *q = nullptr;
+    DILBM_CUDA(cudaMalloc(&q, sizeof(double) * 9 * (size_t)c->L.nx * c->L.ny));
+    c->owned[c->nowned++] = q;
+    c->pops = (double *)q;
+    return DILBM_OK;
+}
+
+int dilbm_get_populations(dilbm_ctx *c, double *f) {
+    if (!c || !f) return fail(DILBM_ERR_INVALID_ARG, "NULL argument");
+    int rc = ensure_pops(c);
+    if (rc) return rc;
+    const int blocks = 152 * 8;
+    switch (c->storage) {
+    case DILBM_FP32: export_kernel<float><<<blocks, 256, 0, c->stream>>>((const float *)c->buf[c->cur], c->L, c->pops); break;
+    case DILBM_FP16_DEV: export_kernel<__half><<<blocks, 256, 0, c->stream>>>((const __half *)c->buf[c->cur], c->L, c->pops); break;
+    default: export_kernel<__nv_bfloat16><<<blocks, 256, 0, c->stream>>>((const __nv_bfloat16 *)c->buf[c->cur], c->L, c->pops); break;
+    }
+    DILBM_CUDA(cudaGetLastError());
+    c->launches += 1;
+    DILBM_CUDA(cudaMemcpyAsync(f, c->pops, sizeof(double) * 9 * (size_t)c->L.nx * c->L.ny, cudaMemcpyDeviceToHost, c->stream));
+    DILBM_CUDA(cudaStreamSynchronize(c->stream));
+    return DILBM_OK;
+}
+
+int dilbm_set_populations(dilbm_ctx *c, const double *f) {
+    if (!c || !f) return fail(DILBM_ERR_INVALID_ARG, "NULL argument");
+    int rc = ensure_pops(c);
+    if (rc) return rc;
+    DILBM_CUDA(cudaMemcpyAsync(c->pops, f, sizeof(double) * 9 * (size_t)c->L.nx * c->L.ny, cudaMemcpyHostToDevice, c->stream));
+    const int blocks = 152 * 8;
+    switch (c->storage) {
+    case DILBM_FP32: import_kernel<float><<<blocks, 256, 0, c->stream>>>((float *)c->buf[c->cur], c->L, c->pops); break;
+    case DILBM_FP16_DEV: import_kernel<__half><<<blocks, 256, 0, c->stream>>>((__half *)c->buf[c->cur], c->L, c->pops); break;
+    default: import_kernel<__nv_bfloat16><<<blocks, 256, 0, c->stream>>>((__nv_bfloat16 *)c->buf[c->cur], c->L, c->pops); break;
+    }
+    DILBM_CUDA(cudaGetLastError());
+    c->launches += 1;
+    DILBM_CUDA(cudaStreamSynchronize(c->stream));
+    return DILBM_OK;
+}
+
+int dilbm_set_particles(dilbm_ctx *c, const dilbm_particle *p, int np) {
+    if (!c || np != c->np || (np > 0 && !p)) return fail(DILBM_ERR_INVALID_ARG, "particle count differs from create");
+    dilbm_grid g{};
+    g.nx = c->L.nx;
+    g.ny = c->L.ny;
+    g.west.kind = g.east.kind = c->L.per_x ? DILBM_SIDE_PERIODIC : DILBM_SIDE_VELOCITY;
+    g.south.kind = g.north.kind = c->L.per_y ? DILBM_SIDE_PERIODIC : DILBM_SIDE_VELOCITY;
+    int rc = check_particles(&g, p, np);
+    if (rc) return rc;
+    return np > 0 ? upload_particles(c, p, np) : DILBM_OK;
+}
+
+void dilbm_destroy(dilbm_ctx *c) {
+    if (!c) return;
+    cudaStreamSynchronize(c->stream);
+    for (int k = 0; k < c->nowned; ++k) cudaFree(c->owned[k]);
+    for (cudaEvent_t e : c->ev) cudaEventDestroy(e);
+    delete c;
+}
+
+int dilbm_set_timing(dilbm_ctx *c, int enable) {
+    if (!c) return fail(DILBM_ERR_INVALID_ARG, "NULL context");
+    DILBM_CUDA(cudaStreamSynchronize(c->stream));
+    c->timing = enable != 0;
+    c->ev_used = 0;
+    return DILBM_OK;
+}
+
+int dilbm_sweep_time(dilbm_ctx *c, double *ms_total, long long *launches) {
+    if (!c || !ms_total || !launches) return fail(DILBM_ERR_INVALID_ARG, "NULL argument");
+    DILBM_CUDA(cudaStreamSynchronize(c->stream));
+    double total = 0.0;
+    for (size_t k = 0; k + 1 < c->ev_used; k += 2) {
+        float ms = 0.f;
+        DILBM_CUDA(cudaEventElapsedTime(&ms, c->ev[k], c->ev[k + 1]));
+        total += ms;
+    }
+    *ms_total = total;
+    *launches = (long long)(c->ev_used / 2);
+    return DILBM_OK;
+}
+
+long long dilbm_launch_count(const dilbm_ctx *c) { return c ? c->launches : -1; }
+
+}  // extern "C"

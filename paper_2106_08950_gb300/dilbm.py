@@ -1,0 +1,250 @@
+"""Python binding of the C ABI in ``include/dilbm.h``.
+
+Argument marshalling only: every step of the DI-LBM path runs in the CUDA
+library ``libdilbm.so``.  The binding refuses to work when that library is
+missing or cannot be loaded; there is no CPU fallback.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+from typing import Optional
+
+import numpy as np
+
+from . import workloads as W
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libdilbm.so")
+
+OK = 0
+ERR_INVALID_ARG = -1
+ERR_OOM = -2
+ERR_CUDA = -3
+ERR_UNSTABLE = -4
+ERR_TIMEOUT = -5
+ERR_OVERFLOW = -6
+MAX_CANDIDATES = 32
+
+FP32, FP16_DEV, BF16_DEV = 0, 1, 2
+STORAGE = {"fp32": FP32, "fp16": FP16_DEV, "bf16": BF16_DEV}
+SIDE = {W.PERIODIC: 0, W.VELOCITY: 1, W.PRESSURE: 2}
+
+
+class DilbmError(RuntimeError):
+    def __init__(self, code: int, msg: str):
+        super().__init__(f"dilbm error {code}: {msg}")
+        self.code = code
+
+
+class Side(C.Structure):
+    _fields_ = [("kind", C.c_int), ("ux", C.c_double), ("uy", C.c_double), ("rho", C.c_double)]
+
+
+class Grid(C.Structure):
+    _fields_ = [("nx", C.c_int), ("ny", C.c_int),
+                ("west", Side), ("east", Side), ("south", Side), ("north", Side),
+                ("gravity", C.c_double * 2), ("rho_f", C.c_double), ("rho_init", C.c_double),
+                ("u0", C.c_double * 2), ("storage", C.c_int), ("force_model", C.c_int),
+                ("wan_turek", C.c_double * 5)]
+
+
+class Particle(C.Structure):
+    _fields_ = [("x", C.c_double), ("y", C.c_double), ("r", C.c_double),
+                ("ux", C.c_double), ("uy", C.c_double), ("omega", C.c_double),
+                ("theta", C.c_double), ("rho_s", C.c_double), ("fixed", C.c_int)]
+
+
+_lib = None
+
+
+def load_library(path: Optional[str] = None):
+    """Load ``libdilbm.so`` (building it in-tree first if it is missing or
+    older than its sources) and declare the C signatures."""
+    global _lib
+    if _lib is not None and path is None:
+        return _lib
+    if path is None:
+        from . import build as _build
+        if _build.stale():
+            _build.build()
+        path = LIB_PATH
+    if not os.path.exists(path):
+        raise RuntimeError(f"CUDA library not found at {path}: run paper_2106_08950_gb300.build")
+    L = C.CDLL(path)
+    vp, ip, dp, fp = C.c_void_p, C.c_int, C.POINTER(C.c_double), C.POINTER(C.c_float)
+    L.dilbm_create.argtypes = [C.POINTER(Grid), ip, C.c_double, C.c_double, C.POINTER(Particle), ip, vp,
+                               C.POINTER(vp)]
+    L.dilbm_step.argtypes = [vp, C.c_longlong]
+    L.dilbm_forces.argtypes = [vp, vp, vp, vp]
+    L.dilbm_fields.argtypes = [vp, vp, vp, vp, vp, ip]
+    L.dilbm_get_populations.argtypes = [vp, vp]
+    L.dilbm_set_populations.argtypes = [vp, vp]
+    L.dilbm_set_particles.argtypes = [vp, C.POINTER(Particle), ip]
+    L.dilbm_sync.argtypes = [vp]
+    L.dilbm_destroy.argtypes = [vp]
+    L.dilbm_destroy.restype = None
+    L.dilbm_last_error.restype = C.c_char_p
+    L.dilbm_set_timing.argtypes = [vp, ip]
+    L.dilbm_sweep_time.argtypes = [vp, dp, C.POINTER(C.c_longlong)]
+    L.dilbm_launch_count.argtypes = [vp]
+    L.dilbm_launch_count.restype = C.c_longlong
+    for name in ("dilbm_create", "dilbm_step", "dilbm_forces", "dilbm_fields", "dilbm_get_populations",
+                 "dilbm_set_populations", "dilbm_set_particles", "dilbm_sync", "dilbm_set_timing",
+                 "dilbm_sweep_time"):
+        getattr(L, name).restype = C.c_int
+    if path == LIB_PATH:
+        _lib = L
+    return L
+
+
+def check(rc: int) -> None:
+    if rc != OK:
+        raise DilbmError(rc, load_library().dilbm_last_error().decode(errors="replace"))
+
+
+def _side(s: W.Side) -> Side:
+    return Side(SIDE[s.kind], s.ux, s.uy, s.rho)
+
+
+def make_grid(prob: W.Problem, storage: str = "fp32") -> Grid:
+    g = Grid()
+    g.nx, g.ny = prob.nx, prob.ny
+    g.west, g.east, g.south, g.north = (_side(prob.west), _side(prob.east), _side(prob.south), _side(prob.north))
+    g.gravity[0], g.gravity[1] = prob.gravity
+    g.rho_f = prob.rho_f
+    g.rho_init = prob.rho_init
+    g.u0[0], g.u0[1] = prob.u0
+    g.storage = STORAGE[storage]
+    g.force_model = prob.force_model
+    for k in range(5):
+        g.wan_turek[k] = prob.wan_turek[k]
+    return g
+
+
+def make_particles(parts) -> "C.Array":
+    arr = (Particle * max(1, len(parts)))()
+    for k, q in enumerate(parts):
+        arr[k] = Particle(q.x, q.y, q.r, q.ux, q.uy, q.omega, q.theta, q.rho_s, int(q.fixed))
+    return arr
+
+
+def particles_to_array(arr, n) -> np.ndarray:
+    """(n, 8) float64: x, y, r, ux, uy, omega, theta, rho_s."""
+    out = np.zeros((n, 8))
+    for k in range(n):
+        q = arr[k]
+        out[k] = (q.x, q.y, q.r, q.ux, q.uy, q.omega, q.theta, q.rho_s)
+    return out
+
+
+def current_stream_handle() -> int:
+    import torch
+    return int(torch.cuda.current_stream().cuda_stream)
+
+
+class Simulation:
+    """One DI-LBM lattice on the GPU (``dilbm_create`` .. ``dilbm_destroy``).
+
+    ``stream``: an integer ``cudaStream_t`` (e.g. ``torch.cuda.Stream().cuda_stream``);
+    None uses torch's current stream.
+    """
+
+    def __init__(self, prob: W.Problem, storage: str = "fp32", stream: Optional[int] = None):
+        self.L = load_library()
+        self.prob = prob
+        self.storage = storage
+        self.np = len(prob.particles)
+        if stream is None:
+            stream = current_stream_handle()
+        self.stream = stream
+        self._grid = make_grid(prob, storage)
+        self._parts = make_particles(prob.particles)
+        h = C.c_void_p()
+        check(self.L.dilbm_create(C.byref(self._grid), 0, prob.tau, prob.eps, self._parts, self.np,
+                                  C.c_void_p(stream), C.byref(h)))
+        self.h = h
+
+    # -- lifetime
+    def close(self) -> None:
+        if getattr(self, "h", None) is not None and self.h.value:
+            self.L.dilbm_destroy(self.h)
+        self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+    # -- stepping
+    def step(self, n: int = 1) -> None:
+        check(self.L.dilbm_step(self.h, int(n)))
+
+    def sync(self) -> None:
+        check(self.L.dilbm_sync(self.h))
+
+    # -- outputs
+    def forces(self):
+        """(np, 3) Fx, Fy, T of the last step; (np, 2) Wan-Turek force; (np, 8) state."""
+        n = max(1, self.np)
+        F = np.zeros((n, 3))
+        Fc = np.zeros((n, 2))
+        st = (Particle * n)()
+        check(self.L.dilbm_forces(self.h, F.ctypes.data, Fc.ctypes.data, C.cast(st, C.c_void_p)))
+        return F[: self.np], Fc[: self.np], particles_to_array(st, self.np)
+
+    def forces_into(self, F: np.ndarray) -> None:
+        """Copy Fx, Fy, T of the last step into a host array of np x 3 doubles."""
+        check(self.L.dilbm_forces(self.h, F.ctypes.data, None, None))
+
+    def fields(self):
+        """rho, ux, uy, phi as (ny, nx) float32 host arrays."""
+        sh = (self.prob.ny, self.prob.nx)
+        out = [np.empty(sh, dtype=np.float32) for _ in range(4)]
+        check(self.L.dilbm_fields(self.h, *[o.ctypes.data for o in out], 0))
+        return tuple(out)
+
+    def fields_device(self, rho=None, ux=None, uy=None, phi=None) -> None:
+        """Write the fields into caller-owned device buffers (torch float32
+        tensors of ny x nx, or None)."""
+        ptr = [t.data_ptr() if t is not None else None for t in (rho, ux, uy, phi)]
+        check(self.L.dilbm_fields(self.h, *ptr, 1))
+
+    def populations(self) -> np.ndarray:
+        out = np.empty((9, self.prob.ny, self.prob.nx))
+        check(self.L.dilbm_get_populations(self.h, out.ctypes.data))
+        return out
+
+    def set_populations(self, f: np.ndarray) -> None:
+        f = np.ascontiguousarray(f, dtype=np.float64)
+        assert f.size == 9 * self.prob.nx * self.prob.ny
+        check(self.L.dilbm_set_populations(self.h, f.ctypes.data))
+
+    def set_particles(self, parts) -> None:
+        self._parts = make_particles(parts)
+        check(self.L.dilbm_set_particles(self.h, self._parts, len(parts)))
+
+    def set_particles_raw(self, arr) -> None:
+        """``arr``: a ctypes array of Particle (e.g. in pinned memory)."""
+        check(self.L.dilbm_set_particles(self.h, arr, self.np))
+
+    # -- measurement
+    def set_timing(self, on: bool) -> None:
+        check(self.L.dilbm_set_timing(self.h, 1 if on else 0))
+
+    def sweep_time(self):
+        ms = C.c_double()
+        n = C.c_longlong()
+        check(self.L.dilbm_sweep_time(self.h, C.byref(ms), C.byref(n)))
+        return ms.value, n.value
+
+    @property
+    def launches(self) -> int:
+        return int(self.L.dilbm_launch_count(self.h))

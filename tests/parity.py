@@ -1,0 +1,47 @@
+"""Comparison helpers shared by the GPU parity tests (CUDA path vs oracle)."""
+import numpy as np
+
+# FP32 path: relative L2 of the velocity field and relative drag / absolute
+# lift-coefficient error against the FP64 oracle.
+TOL_FP32 = 1e-5
+# FP16 / BF16 deviation storage: drag-coefficient error bound.
+TOL_REDUCED_DRAG = 1e-3
+
+
+def rel_l2_velocity(g, o):
+    """Relative L2 norm of the velocity difference over all nodes."""
+    gx, gy = np.asarray(g[1], np.float64), np.asarray(g[2], np.float64)
+    ox, oy = o[1], o[2]
+    num = np.sqrt(((gx - ox) ** 2 + (gy - oy) ** 2).sum())
+    den = np.sqrt((ox ** 2 + oy ** 2).sum())
+    return num / den
+
+
+def compare_fields(g, o, tol=TOL_FP32):
+    """g: (rho, ux, uy, phi) float32 from the GPU; o: the oracle's fields."""
+    errs = {
+        "vel_rel_l2": rel_l2_velocity(g, o),
+        "rho_max_abs": float(np.abs(g[0] - o[0]).max()),
+        "phi_max_abs": float(np.abs(g[3] - o[3]).max()),
+    }
+    ok = errs["vel_rel_l2"] <= tol and errs["rho_max_abs"] <= tol and errs["phi_max_abs"] <= tol
+    return ok, errs
+
+
+def compare_forces(Fg, Fo, tol=TOL_FP32):
+    """Per-particle force and torque, relative to the largest force magnitude
+    (the torque relative to the largest force times the largest radius is
+    checked by the caller when needed)."""
+    scale = max(np.abs(Fo[:, :2]).max(), 1e-30)
+    err_f = float(np.abs(Fg[:, :2] - Fo[:, :2]).max() / scale)
+    tscale = max(np.abs(Fo[:, 2]).max(), scale)
+    err_t = float(np.abs(Fg[:, 2] - Fo[:, 2]).max() / tscale)
+    return err_f <= tol and err_t <= tol, {"force_rel": err_f, "torque_rel": err_t}
+
+
+def compare_state(Sg, So, tol_pos=1e-6, tol_vel=1e-5):
+    """Particle state (x, y, r, ux, uy, omega, theta, rho_s)."""
+    dpos = float(np.abs(Sg[:, :2] - So[:, :2]).max()) if len(So) else 0.0
+    vscale = max(np.abs(So[:, 3:5]).max(), 1e-30) if len(So) else 1.0
+    dvel = float(np.abs(Sg[:, 3:5] - So[:, 3:5]).max() / vscale) if len(So) else 0.0
+    return dpos <= tol_pos and dvel <= tol_vel, {"pos_abs": dpos, "vel_rel": dvel}

@@ -1,0 +1,237 @@
+"""CUDA path vs FP64 oracle on the same seeded inputs, through the C ABI.
+
+Every case compares element by element (fields at every node, every
+particle's force, torque and state) within the FP32 tolerance 1e-5 (relative
+L2 of the velocity, relative drag, absolute lift coefficient).
+"""
+import math
+import os
+
+import numpy as np
+import pytest
+
+from oracle import oracle as O
+from paper_2106_08950_gb300 import dilbm as D
+from paper_2106_08950_gb300 import workloads as W
+from tests import parity as PAR
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def stream():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    D.load_library()
+    s = torch.cuda.Stream()
+    return int(s.cuda_stream)
+
+
+def run_both(prob, steps, stream, storage="fp32", cutoff=0.0, chunks=1):
+    g = D.Simulation(prob, storage=storage, stream=stream)
+    o = O.OracleSim(prob, phi_cutoff=cutoff)
+    per = steps // chunks
+    for _ in range(chunks):
+        g.step(per)
+        o.step(per)
+    g.sync()
+    return g, o
+
+
+def assert_parity(g, o, tol=PAR.TOL_FP32, check_state=True):
+    ok, errs = PAR.compare_fields(g.fields(), o.fields(), tol)
+    assert ok, errs
+    if g.np:
+        Fg, _, Sg = g.forces()
+        Fo, _, So = o.forces()
+        ok, e2 = PAR.compare_forces(Fg, Fo, tol)
+        assert ok, e2
+        if check_state:
+            ok, e3 = PAR.compare_state(Sg, So)
+            assert ok, e3
+
+
+def moving_particles(nx=160, ny=40):
+    return W.Problem(nx=nx, ny=ny, tau=0.7, eps=2.0, u0=(0.01, -0.004), gravity=(0.0, -2e-5),
+                     wan_turek=W.wan_turek_defaults(5.0, 1.3, 1.0, 2e-5),
+                     particles=[W.Particle(20.3, 12.7, 6.0, ux=0.02, uy=0.01, omega=0.002, rho_s=1.3),
+                                W.Particle(90.6, 27.4, 5.0, ux=-0.01, uy=0.015, omega=-0.001, rho_s=1.1),
+                                W.Particle(151.2, 3.1, 4.5, ux=0.005, rho_s=1.6)])
+
+
+def test_periodic_moving_particles(stream):
+    # Two tiles in x (128 + 32 nodes), five in y; one disc straddles both edges.
+    g, o = run_both(moving_particles(), 300, stream)
+    assert_parity(g, o)
+
+
+def test_ragged_lattice_not_multiple_of_four(stream):
+    prob = moving_particles(nx=130, ny=21)
+    prob.particles = [W.Particle(128.4, 10.3, 4.0, ux=0.01, omega=0.003, rho_s=1.2),
+                      W.Particle(50.5, 9.5, 5.0, uy=-0.01, rho_s=1.4)]
+    g, o = run_both(prob, 200, stream)
+    assert_parity(g, o)
+
+
+@pytest.mark.parametrize("fm", [W.FORCE_EQ18, W.FORCE_MOMENTUM])
+def test_cylinder_drag_full_run(stream, fm):
+    # 200 x 100, r = 10 at (50, 50), inlet U = 0.05, Re = 20, 2000 steps.
+    prob = W.cylinder_drag(force_model=fm)
+    g, o = run_both(prob, 2000, stream)
+    Fg, _, _ = g.forces()
+    Fo, _, _ = o.forces()
+    q = 0.5 * 1.0 * 20.0 * 0.05 ** 2
+    cd_g, cd_o = Fg[0, 0] / q, Fo[0, 0] / q
+    cl_g, cl_o = Fg[0, 1] / q, Fo[0, 1] / q
+    assert abs(cd_g - cd_o) / abs(cd_o) <= PAR.TOL_FP32, (cd_g, cd_o)
+    assert abs(cl_g - cl_o) <= PAR.TOL_FP32, (cl_g, cl_o)
+    ok, errs = PAR.compare_fields(g.fields(), o.fields())
+    assert ok, errs
+
+
+@pytest.mark.parametrize("fm", [W.FORCE_EQ18, W.FORCE_MOMENTUM])
+def test_closed_box_settling_near_wall(stream, fm):
+    # Four extrapolated walls (corners included) and Wan-Turek wall contact:
+    # the disc starts 0.3 lu beyond contact with the west wall.
+    prob = W.sedimentation(nx=64, ny=96, r=6.0, rho_s=1.5, g=2e-5, force_model=fm, x0=6.3, y0=60.0)
+    g, o = run_both(prob, 600, stream)
+    _, Fc, _ = o.forces()
+    assert abs(Fc[0, 0]) > 0.0          # the wall repulsion acts during the run
+    assert_parity(g, o)
+
+
+def test_pressure_driven_channel(stream):
+    prob = W.Problem(nx=150, ny=33, tau=1.1, eps=2.0,
+                     west=W.Side(W.PRESSURE, rho=1.0005), east=W.Side(W.PRESSURE, rho=0.9995),
+                     south=W.wall(), north=W.wall())
+    g, o = run_both(prob, 1500, stream)
+    assert_parity(g, o)
+
+
+def test_velocity_walls_couette(stream):
+    prob = W.Problem(nx=37, ny=17, tau=0.8, eps=2.0, south=W.wall(), north=W.wall(0.01, 0.0))
+    g, o = run_both(prob, 3000, stream)
+    assert_parity(g, o)
+
+
+def test_no_particles(stream):
+    prob2, prof = W.shear_wave(n=64, amp=1e-3, tau=0.9, nx=64)
+    f0 = np.stack([np.tile(O.equilibrium(1.0, u, 0.0), (prob2.nx, 1)).T for u in prof], axis=1)
+    g = D.Simulation(prob2, stream=stream)
+    o = O.OracleSim(prob2)
+    g.set_populations(f0)
+    o.set_populations(f0)
+    g.step(500)
+    o.step(500)
+    assert_parity(g, o)
+
+
+def test_downscaled_periodic_suspension(stream):
+    # 512^2 periodic box, 32 discs, the same radius / density distributions as
+    # the 4096^2 workload, 2000 steps.
+    prob = W.periodic_suspension(n=512, count=32, seed=3)
+    g, o = run_both(prob, 2000, stream, chunks=4)
+    assert_parity(g, o)
+
+
+def test_full_size_periodic_suspension_sampled(stream):
+    # The benchmark workload itself (4096^2, 2048 discs) for 6 steps in the
+    # same launch configuration; the oracle uses its 6-width phi cutoff.
+    prob = W.periodic_suspension()
+    o = O.OracleSim(prob, phi_cutoff=6 * prob.eps)
+    g = D.Simulation(prob, stream=stream)
+    g.step(6)
+    o.step(6)
+    g.sync()
+    Fg, _, Sg = g.forces()
+    Fo, _, So = o.forces()
+    ok, e = PAR.compare_forces(Fg, Fo)
+    assert ok, e
+    ok, e = PAR.compare_state(Sg, So)
+    assert ok, e
+    gf, of = g.fields(), o.fields()
+    rng = np.random.default_rng(0)
+    idx = rng.integers(0, prob.nx * prob.ny, size=200000)
+    sub = lambda f: [a.ravel()[idx] for a in f[:4]]
+    ok, errs = PAR.compare_fields(sub(gf), sub(of))
+    assert ok, errs
+    # nodes near particles, where the coupling acts
+    near = np.flatnonzero(of[3].ravel() > 1e-3)[::7]
+    ok, errs = PAR.compare_fields([a.ravel()[near] for a in gf[:4]], [a.ravel()[near] for a in of[:4]])
+    assert ok, errs
+
+
+def test_fields_into_device_tensors(stream):
+    import torch
+    prob = moving_particles()
+    g = D.Simulation(prob, stream=stream)
+    g.step(20)
+    t = [torch.empty((prob.ny, prob.nx), dtype=torch.float32, device="cuda") for _ in range(4)]
+    g.fields_device(*t)
+    torch.cuda.synchronize()
+    host = g.fields()
+    for a, b in zip(t, host):
+        assert np.array_equal(a.cpu().numpy(), b)
+
+
+def test_checkpoint_resume_bitwise(stream):
+    prob = moving_particles()
+    a = D.Simulation(prob, stream=stream)
+    a.step(50)
+    f = a.populations()
+    _, _, st = a.forces()
+    a.step(50)
+    Fa, _, Sa = a.forces()
+    b = D.Simulation(prob, stream=stream)
+    b.set_populations(f)
+    parts = [W.Particle(*row[:8], fixed=q.fixed) for row, q in zip(st, prob.particles)]
+    b.set_particles(parts)
+    b.step(50)
+    Fb, _, Sb = b.forces()
+    assert np.array_equal(Fa, Fb) and np.array_equal(Sa, Sb)
+    assert np.array_equal(a.populations(), b.populations())
+
+
+def test_runs_are_deterministic(stream):
+    prob = W.periodic_suspension(n=512, count=32, seed=9)
+    r = []
+    for _ in range(2):
+        g = D.Simulation(prob, stream=stream)
+        g.step(100)
+        r.append(g.forces())
+    assert np.array_equal(r[0][0], r[1][0]) and np.array_equal(r[0][2], r[1][2])
+
+
+def test_tile_overflow_is_reported(stream):
+    # 40 tiny discs inside one 128 x 8 tile: more than the 32 candidates a tile
+    # holds.  The step reports DILBM_ERR_OVERFLOW instead of a wrong result.
+    parts = [W.Particle(4.0 + 3.0 * k, 4.0, 0.5, rho_s=2.0) for k in range(40)]
+    prob = W.Problem(nx=256, ny=64, tau=0.8, eps=1.0, particles=parts)
+    g = D.Simulation(prob, stream=stream)
+    g.step(1)
+    with pytest.raises(D.DilbmError) as e:
+        g.sync()
+    assert e.value.code == D.ERR_OVERFLOW
+
+
+def test_instability_is_reported(stream):
+    prob = W.Problem(nx=64, ny=64, tau=0.5001, eps=2.0, u0=(0.9, 0.7))
+    g = D.Simulation(prob, stream=stream)
+    g.step(400)
+    with pytest.raises(D.DilbmError) as e:
+        g.sync()
+    assert e.value.code == D.ERR_UNSTABLE
+
+
+@pytest.mark.parametrize("storage", ["fp16", "bf16"])
+def test_reduced_precision_drag(stream, storage):
+    # Deviation storage in FP16 / BF16 with FP32 arithmetic: the drag
+    # coefficient stays within 1e-3 of the FP64 oracle over the full run.
+    prob = W.cylinder_drag()
+    g, o = run_both(prob, 2000, stream, storage=storage)
+    Fg, _, _ = g.forces()
+    Fo, _, _ = o.forces()
+    err = abs(Fg[0, 0] - Fo[0, 0]) / abs(Fo[0, 0])
+    print(f"{storage} drag error {err:.3e}")
+    assert err <= PAR.TOL_REDUCED_DRAG
