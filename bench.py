@@ -160,7 +160,7 @@ def barrier(dist):
 def oracle_mlups(prob, seconds: float, max_steps: int = 1_000_000, min_steps: int = 2):
     """Time the FP64 oracle as it stands on all host cores."""
     from oracle import oracle as O
-    sim = O.OracleSim(prob, phi_cutoff=6 * prob.eps)
+    sim = O.OracleSim(prob, phi_cutoff=4 * prob.eps)
     sim.step(1)                      # warm-up: first-touch of the arrays
     t0 = time.perf_counter()
     n = 0
@@ -183,7 +183,7 @@ def reference_arm(args):
     count = max(1, round(len(prob.particles) * (n_small / max(prob.nx, 1)) ** 2)) if args.workload == "periodic" else 0
     small = (W.periodic_suspension(n=n_small, count=count, seed=3) if args.workload == "periodic" else prob)
     from oracle import oracle as O
-    sim = O.OracleSim(small, phi_cutoff=6 * small.eps)
+    sim = O.OracleSim(small, phi_cutoff=4 * small.eps)
     for _ in range(args.warmup):
         sim.step(1)
     t0 = time.perf_counter()
@@ -319,7 +319,7 @@ def gpu_arm(args):
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         v, n, dt, cores = oracle_mlups(prob, args.cpu_seconds)
         line["cpu_baseline"] = {"value": v, "unit": "MLUPS", "cores": cores, "kind": "oracle",
-                                "sample": f"{n} steps of the full workload ({dt:.1f} s), phi cutoff 6 widths"}
+                                "sample": f"{n} steps of the full workload ({dt:.1f} s), phi cutoff 4 widths"}
     if rank == 0:
         print(json.dumps(line), flush=True)
     sim.close()

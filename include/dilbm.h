@@ -40,7 +40,7 @@ extern "C" {
 #define DILBM_ERR_TIMEOUT     (-5)  /* a bounded device-side wait gave up */
 #define DILBM_ERR_OVERFLOW    (-6)  /* more than DILBM_MAX_CANDIDATES particles near one tile */
 
-/* Particles whose (radius + 6 interface widths) disc reaches one lattice tile
+/* Particles whose (radius + 4 interface widths) disc reaches one lattice tile
  * (128 x 8 nodes); more is reported as DILBM_ERR_OVERFLOW. */
 #define DILBM_MAX_CANDIDATES 32
 

@@ -122,8 +122,8 @@ def particles_to_array(arr, n) -> np.ndarray:
 
 class OracleSim:
     """FP64 DI-LBM on the host.  ``phi_cutoff`` > 0 skips, at each node, the
-    particles whose signed distance is below -phi_cutoff (phi < 4e-11 at
-    6 interface widths); 0 evaluates every particle at every node."""
+    particles whose signed distance is below -phi_cutoff (phi < 1.1e-7 beyond
+    4 interface widths); 0 evaluates every particle at every node."""
 
     def __init__(self, prob, phi_cutoff: float = 0.0, threads: int = 0):
         self.L = lib()

@@ -42,7 +42,8 @@ struct dilbm_ctx {
     void *buf[2] = {nullptr, nullptr};
     int cur = 0;
     Particles P{};
-    Bins B{};
+    Bins bins[2]{};                   // tile bins by step parity
+    float4 *partial = nullptr;        // per tile, slot and row: force / torque partials
     double *force = nullptr, *fcol = nullptr;
     int *err = nullptr;
     int sticky = 0;
@@ -51,11 +52,12 @@ struct dilbm_ctx {
     cudaStream_t stream = nullptr;
     int np = 0;
     int ntiles = 0;
+    int num_sms = 1;
     bool timing = false;
     std::vector<cudaEvent_t> ev;      // start/stop pairs around sweep launches
     size_t ev_used = 0;
     long long launches = 0;
-    void *owned[16] = {};
+    void *owned[32] = {};
     int nowned = 0;
 };
 
@@ -93,7 +95,44 @@ int check_particles(const dilbm_grid *g, const dilbm_particle *p, int np) {
     return DILBM_OK;
 }
 
+// A tile's nodes share the particle image nearest the tile centre unless the
+// periodic axis is shorter than the tile plus two reach radii.
+void set_wrap_flags(dilbm_ctx *c, const dilbm_particle *p, int np) {
+    double rmax = 0.0;
+    for (int k = 0; k < np; ++k) rmax = p[k].r > rmax ? p[k].r : rmax;
+    const double reach = 2.0 * (rmax + c->ph.cut_d) + 2.0;
+    c->L.wrap_x = c->L.per_x && c->L.nx < reach + TILE_W;
+    c->L.wrap_y = c->L.per_y && c->L.ny < reach + TILE_H;
+}
+
+int check_reach(dilbm_ctx *c, const dilbm_particle *p, int np) {
+    // tiles one particle's phi tail may reach must fit the per-particle map
+    for (int k = 0; k < np; ++k) {
+        const double R = p[k].r + c->ph.cut_d;
+        const long long tx = (long long)std::ceil((2.0 * R + 2.0) / TILE_W) + 1;
+        const long long ty = (long long)std::ceil((2.0 * R + 2.0) / TILE_H) + 1;
+        if (tx * ty > MAXT)
+            return fail(DILBM_ERR_INVALID_ARG, "particle " + std::to_string(k) +
+                                                   " is too large: its phi tail would reach more than " +
+                                                   std::to_string(MAXT) + " lattice tiles");
+    }
+    return DILBM_OK;
+}
+
+int launch_particles(dilbm_ctx *c, int integrate) {
+    const int np = c->np, cur = c->cur, nxt = integrate ? cur ^ 1 : cur;
+    particles_kernel<<<(np * 32 + 127) / 128, 128, 0, c->stream>>>(
+        c->L, c->ph, c->P, c->bp, c->bins[cur], c->bins[nxt], c->partial, cur, nxt, integrate, c->force, c->fcol,
+        c->err);
+    DILBM_CUDA(cudaGetLastError());
+    c->launches += 1;
+    return DILBM_OK;
+}
+
 int upload_particles(dilbm_ctx *c, const dilbm_particle *p, int np) {
+    set_wrap_flags(c, p, np);
+    int rc = check_reach(c, p, np);
+    if (rc) return rc;
     std::vector<double> h(8 * (size_t)np);
     std::vector<int> fx(np);
     for (int k = 0; k < np; ++k) {
@@ -102,37 +141,63 @@ int upload_particles(dilbm_ctx *c, const dilbm_particle *p, int np) {
         h[6 * np + k] = p[k].theta; h[7 * np + k] = p[k].rho_s;
         fx[k] = p[k].fixed ? 1 : 0;
     }
-    // P.x .. P.rho_s are consecutive slices of one allocation
-    DILBM_CUDA(cudaMemcpyAsync(c->P.x, h.data(), sizeof(double) * h.size(), cudaMemcpyHostToDevice, c->stream));
+    const int cur = c->cur;
+    DILBM_CUDA(cudaMemcpyAsync(c->P.x[cur], h.data(), sizeof(double) * np, cudaMemcpyHostToDevice, c->stream));
+    DILBM_CUDA(cudaMemcpyAsync(c->P.y[cur], h.data() + np, sizeof(double) * np, cudaMemcpyHostToDevice, c->stream));
+    // r, ux, uy, omega, theta, rho_s are consecutive slices of one allocation
+    DILBM_CUDA(cudaMemcpyAsync(c->P.r, h.data() + 2 * np, sizeof(double) * 6 * np, cudaMemcpyHostToDevice, c->stream));
     DILBM_CUDA(cudaMemcpyAsync(c->P.fixed, fx.data(), sizeof(int) * np, cudaMemcpyHostToDevice, c->stream));
-    DILBM_CUDA(cudaMemsetAsync(c->B.count, 0, sizeof(int) * c->ntiles, c->stream));
-    integrate_bin_kernel<<<(np + 127) / 128, 128, 0, c->stream>>>(c->L, c->ph, c->P, c->B, c->bp,
-                                                                  c->force, c->fcol, 0, c->err);
-    DILBM_CUDA(cudaGetLastError());
-    c->launches += 1;
+    DILBM_CUDA(cudaMemsetAsync(c->bins[cur].count, 0, sizeof(int) * c->ntiles, c->stream));
+    if ((rc = launch_particles(c, 0))) return rc;
     // the host copies above read pageable memory that goes out of scope
     DILBM_CUDA(cudaStreamSynchronize(c->stream));
     return DILBM_OK;
 }
 
+// Persistent grid: as many blocks as fit on the device at once (queried per
+// kernel instantiation), but no more than the row segments need.
+template <typename T, int MODE, bool EDGES>
+cudaError_t launch_sweep_k(dilbm_ctx *c, const void *src, void *dst, FieldsOut fo) {
+    static int per_sm[64] = {};     // blocks per SM, per device ordinal
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    const size_t smem = sweep_smem_bytes<T>();
+    auto kern = sweep_kernel<T, MODE, EDGES>;
+    if (dev < 64 && per_sm[dev] == 0) {
+        e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return e;
+        int n = 0;
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, kern, SWEEP_WARPS * 32, smem);
+        if (e != cudaSuccess) return e;
+        per_sm[dev] = n > 0 ? n : 1;
+    }
+    const long long items = (long long)c->L.ny * c->L.ntx;
+    long long blocks = (long long)c->num_sms * (dev < 64 ? per_sm[dev] : 1);
+    const long long need = (items + SWEEP_WARPS - 1) / SWEEP_WARPS;
+    if (blocks > need) blocks = need;
+    const int cur = c->cur;
+    kern<<<(unsigned)blocks, SWEEP_WARPS * 32, smem, c->stream>>>(
+        (const T *)src, (T *)dst, c->L, c->ph, c->bins[cur], c->partial,
+        (MODE == MODE_STEP && c->np > 0) ? c->bins[cur ^ 1].count : nullptr, fo, c->err);
+    return cudaGetLastError();
+}
+
+template <typename T, int MODE>
+cudaError_t launch_sweep_t(dilbm_ctx *c, const void *src, void *dst, FieldsOut fo) {
+    if (c->L.per_x && c->L.per_y) return launch_sweep_k<T, MODE, false>(c, src, dst, fo);
+    return launch_sweep_k<T, MODE, true>(c, src, dst, fo);
+}
+
 template <int MODE>
 int launch_sweep(dilbm_ctx *c, const void *src, void *dst, FieldsOut fo) {
-    dim3 grid(c->L.ntx, c->L.nty), block(32, TILE_H);
+    cudaError_t e;
     switch (c->storage) {
-    case DILBM_FP32:
-        sweep_kernel<float, MODE><<<grid, block, 0, c->stream>>>(
-            (const float *)src, (float *)dst, c->L, c->ph, c->P, c->B, fo, c->err);
-        break;
-    case DILBM_FP16_DEV:
-        sweep_kernel<__half, MODE><<<grid, block, 0, c->stream>>>(
-            (const __half *)src, (__half *)dst, c->L, c->ph, c->P, c->B, fo, c->err);
-        break;
-    default:
-        sweep_kernel<__nv_bfloat16, MODE><<<grid, block, 0, c->stream>>>(
-            (const __nv_bfloat16 *)src, (__nv_bfloat16 *)dst, c->L, c->ph, c->P, c->B, fo, c->err);
-        break;
+    case DILBM_FP32: e = launch_sweep_t<float, MODE>(c, src, dst, fo); break;
+    case DILBM_FP16_DEV: e = launch_sweep_t<__half, MODE>(c, src, dst, fo); break;
+    default: e = launch_sweep_t<__nv_bfloat16, MODE>(c, src, dst, fo); break;
     }
-    DILBM_CUDA(cudaGetLastError());
+    if (e != cudaSuccess) return cuda_fail(e, "sweep_kernel launch");
     c->launches += 1;
     return DILBM_OK;
 }
@@ -155,17 +220,7 @@ int one_step(dilbm_ctx *c) {
     int rc = launch_sweep<MODE_STEP>(c, c->buf[c->cur], c->buf[c->cur ^ 1], FieldsOut{});
     if (rc) return rc;
     if (c->timing) DILBM_CUDA(cudaEventRecord(e1, c->stream));
-    if (c->np > 0) {
-        const int np = c->np;
-        reduce_kernel<<<(np * 32 + 127) / 128, 128, 0, c->stream>>>(c->L, c->ph, c->P, c->B, c->bp,
-                                                                    c->force, c->fcol);
-        DILBM_CUDA(cudaGetLastError());
-        DILBM_CUDA(cudaMemsetAsync(c->B.count, 0, sizeof(int) * c->ntiles, c->stream));
-        integrate_bin_kernel<<<(np + 127) / 128, 128, 0, c->stream>>>(c->L, c->ph, c->P, c->B, c->bp,
-                                                                      c->force, c->fcol, 1, c->err);
-        DILBM_CUDA(cudaGetLastError());
-        c->launches += 2;
-    }
+    if (c->np > 0 && (rc = launch_particles(c, 1))) return rc;
     c->cur ^= 1;
     return DILBM_OK;
 }
@@ -176,6 +231,7 @@ int read_sticky(dilbm_ctx *c) {
     DILBM_CUDA(cudaStreamSynchronize(c->stream));
     c->sticky |= h;
     if (c->sticky & ERR_UNSTABLE) return fail(DILBM_ERR_UNSTABLE, "a node reached rho <= 0 or a non-finite velocity");
+    if (c->sticky & ERR_TIMEOUT) return fail(DILBM_ERR_TIMEOUT, "a bounded device wait gave up (1 s)");
     if (c->sticky & ERR_OVERFLOW)
         return fail(DILBM_ERR_OVERFLOW, "more than DILBM_MAX_CANDIDATES particles reach one lattice tile");
     return DILBM_OK;
@@ -253,34 +309,49 @@ int dilbm_create(const dilbm_grid *g, dilbm_lattice lattice, double tau, double 
     bp.xi = g->wan_turek[4];
 
     auto bail = [&](int code) { dilbm_destroy(c); return code; };
-    const size_t pop_elems = 9 * (size_t)L.plane;
+    {
+        int dev = 0;
+        cudaError_t e = cudaGetDevice(&dev);
+        if (e == cudaSuccess) e = cudaDeviceGetAttribute(&c->num_sms, cudaDevAttrMultiProcessorCount, dev);
+        if (e != cudaSuccess) return bail(cuda_fail(e, "cudaDeviceGetAttribute"));
+    }
+    // each population buffer carries GUARD readable elements on both sides:
+    // the sweep stages whole 16-byte-aligned row segments with their halos
+    const size_t pop_elems = 9 * (size_t)L.plane + 2 * (size_t)GUARD;
     for (int b = 0; b < 2; ++b) {
         void *q = nullptr;
         cudaError_t e = cudaMalloc(&q, pop_elems * c->elem);
         if (e != cudaSuccess) return bail(cuda_fail(e, "cudaMalloc populations"));
         c->owned[c->nowned++] = q;
-        c->buf[b] = q;
+        c->buf[b] = static_cast<char *>(q) + GUARD * c->elem;
         e = cudaMemsetAsync(q, 0, pop_elems * c->elem, c->stream);
         if (e != cudaSuccess) return bail(cuda_fail(e, "cudaMemsetAsync"));
     }
     const int npa = np > 0 ? np : 1;
     double *pd = nullptr;
     float *pf = nullptr;
-    if ((rc = dev_alloc(c, &pd, 8 * (size_t)npa)) || (rc = dev_alloc(c, &pf, 2 * (size_t)npa)) ||
+    if ((rc = dev_alloc(c, &pd, 10 * (size_t)npa)) || (rc = dev_alloc(c, &pf, 4 * (size_t)npa)) ||
         (rc = dev_alloc(c, &c->P.fixed, (size_t)npa)) || (rc = dev_alloc(c, &c->force, 3 * (size_t)npa)) ||
         (rc = dev_alloc(c, &c->fcol, 2 * (size_t)npa)) || (rc = dev_alloc(c, &c->err, 1)) ||
-        (rc = dev_alloc(c, &c->B.count, (size_t)c->ntiles)) ||
-        (rc = dev_alloc(c, &c->B.ids, (size_t)c->ntiles * MAXC)) ||
-        (rc = dev_alloc(c, &c->B.partial, (size_t)c->ntiles * MAXC * 3)))
+        (rc = dev_alloc(c, &c->partial, (size_t)c->ntiles * MAXC * TILE_H)))
         return bail(rc);
-    c->P.x = pd; c->P.y = pd + npa; c->P.r = pd + 2 * npa; c->P.ux = pd + 3 * npa;
-    c->P.uy = pd + 4 * npa; c->P.omega = pd + 5 * npa; c->P.theta = pd + 6 * npa; c->P.rho_s = pd + 7 * npa;
-    c->P.xf = pf; c->P.yf = pf + npa;
+    for (int b = 0; b < 2; ++b) {
+        Bins &B = c->bins[b];
+        if ((rc = dev_alloc(c, &B.count, (size_t)c->ntiles)) || (rc = dev_alloc(c, &B.ids, (size_t)c->ntiles * MAXC)) ||
+            (rc = dev_alloc(c, &B.rec, (size_t)c->ntiles * MAXC * NREC)) ||
+            (rc = dev_alloc(c, &B.pslot, (size_t)npa * MAXT)) || (rc = dev_alloc(c, &B.npslot, (size_t)npa)))
+            return bail(rc);
+    }
+    c->P.x[0] = pd; c->P.x[1] = pd + npa; c->P.y[0] = pd + 2 * npa; c->P.y[1] = pd + 3 * npa;
+    c->P.r = pd + 4 * npa; c->P.ux = pd + 5 * npa; c->P.uy = pd + 6 * npa; c->P.omega = pd + 7 * npa;
+    c->P.theta = pd + 8 * npa; c->P.rho_s = pd + 9 * npa;
+    c->P.xf[0] = pf; c->P.xf[1] = pf + npa; c->P.yf[0] = pf + 2 * npa; c->P.yf[1] = pf + 3 * npa;
     cudaError_t e;
     if ((e = cudaMemsetAsync(c->err, 0, sizeof(int), c->stream)) != cudaSuccess ||
         (e = cudaMemsetAsync(c->force, 0, sizeof(double) * 3 * npa, c->stream)) != cudaSuccess ||
         (e = cudaMemsetAsync(c->fcol, 0, sizeof(double) * 2 * npa, c->stream)) != cudaSuccess ||
-        (e = cudaMemsetAsync(c->B.count, 0, sizeof(int) * c->ntiles, c->stream)) != cudaSuccess)
+        (e = cudaMemsetAsync(c->bins[0].count, 0, sizeof(int) * c->ntiles, c->stream)) != cudaSuccess ||
+        (e = cudaMemsetAsync(c->bins[1].count, 0, sizeof(int) * c->ntiles, c->stream)) != cudaSuccess)
         return bail(cuda_fail(e, "cudaMemsetAsync"));
     // uniform initial state f^eq(rho_init, u0)
     const int blocks = 152 * 8;
@@ -322,7 +393,9 @@ int dilbm_forces(dilbm_ctx *c, double *force, double *fcol, dilbm_particle *stat
     DILBM_CUDA(cudaMemcpyAsync(force, c->force, sizeof(double) * 3 * np, cudaMemcpyDeviceToHost, c->stream));
     if (fcol) DILBM_CUDA(cudaMemcpyAsync(fcol, c->fcol, sizeof(double) * 2 * np, cudaMemcpyDeviceToHost, c->stream));
     if (state) {
-        DILBM_CUDA(cudaMemcpyAsync(h.data(), c->P.x, sizeof(double) * h.size(), cudaMemcpyDeviceToHost, c->stream));
+        DILBM_CUDA(cudaMemcpyAsync(h.data(), c->P.x[c->cur], sizeof(double) * np, cudaMemcpyDeviceToHost, c->stream));
+        DILBM_CUDA(cudaMemcpyAsync(h.data() + np, c->P.y[c->cur], sizeof(double) * np, cudaMemcpyDeviceToHost, c->stream));
+        DILBM_CUDA(cudaMemcpyAsync(h.data() + 2 * np, c->P.r, sizeof(double) * 6 * np, cudaMemcpyDeviceToHost, c->stream));
         DILBM_CUDA(cudaMemcpyAsync(fx.data(), c->P.fixed, sizeof(int) * np, cudaMemcpyDeviceToHost, c->stream));
     }
     int rc = read_sticky(c);   // synchronises the stream

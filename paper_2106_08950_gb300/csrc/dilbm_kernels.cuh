@@ -1,20 +1,29 @@
 // Device code of the DI-LBM step on sm_103a.
 //
-// One time step (the paper's procedure, Sec. 2.3) is three kernels:
-//   sweep_kernel      -- every node: pull-stream, edge extrapolation, solid
-//                        fraction (Eq. 14), corrected velocity (Eq. 17),
-//                        collision with the force term (Eqs. 13, 15), and the
-//                        node's share of force/torque (Eqs. 18-19) summed per
-//                        tile and per nearby particle into FP64 partials;
-//   reduce_kernel     -- per particle: fixed-order FP64 sum of its partials
-//                        and the Wan-Turek repulsion (Eqs. 28-29);
-//   integrate_bin_kernel -- per particle: Newton-Euler update (Eqs. 22-24),
-//                        then binning of the particle into the lattice tiles
-//                        its phi tail reaches, for the next sweep.
+// One time step (the paper's procedure, Sec. 2.3) is two kernels:
+//   sweep_kernel     -- every node: pull-stream, edge extrapolation, solid
+//                       fraction (Eq. 14), corrected velocity (Eq. 17),
+//                       collision with the force term (Eqs. 13, 15), and the
+//                       node's share of force/torque (Eqs. 18-19) summed per
+//                       row segment and nearby particle;
+//   particles_kernel -- one warp per particle: fixed-order FP64 sum of its
+//                       partials (Eqs. 18-19), Wan-Turek repulsion (Eqs.
+//                       28-29), Newton-Euler update (Eqs. 22-24), then binning
+//                       of the particle into the lattice tiles its phi tail
+//                       reaches, for the next sweep.
 //
 // Populations are stored as deviations d_i = f_i - w_i (structure of arrays:
-// 9 planes of ny rows of `pitch` elements), in FP32, FP16 or BF16; all
-// arithmetic is FP32, force/torque accumulation and particle state FP64.
+// 9 planes of ny rows of `pitch` elements), in FP32, FP16 or BF16; arithmetic
+// is FP32, force/torque accumulation and particle state FP64.  Particle
+// positions and the tile bins are double-buffered by step parity, so a step
+// reads one copy and writes the other.
+//
+// The sweep is a persistent kernel: each warp walks row segments of 128 nodes
+// and streams every segment's nine source rows (plus a 16-byte halo on each
+// side) into a two-stage shared-memory ring with bulk asynchronous copies
+// (cp.async.bulk, completion on an mbarrier), so the next segment's loads are
+// in flight while the current one is collided.  Writes go straight from
+// registers as 16-byte stores.
 #pragma once
 
 #include <cuda_bf16.h>
@@ -24,15 +33,21 @@
 
 namespace dilbm {
 
-constexpr int TILE_W = 128;   // nodes per tile row: 32 lanes x 4 nodes
-constexpr int TILE_H = 8;     // rows per tile: one warp per row
+constexpr int TILE_W = 128;   // nodes per row segment (32 lanes x 4 nodes) and per tile row
+constexpr int TILE_H = 8;     // rows per binning tile
 constexpr int VEC = 4;        // nodes per thread
 constexpr int MAXC = 32;      // candidate particles per tile
-constexpr float PHI_CUT_WIDTHS = 6.0f;   // phi tail kept up to 6 interface widths
+constexpr int MAXT = 128;     // tiles one particle's phi tail may reach
+constexpr int NREC = 3;       // float4 records per binned particle
+constexpr int STAGES = 2;     // shared-memory ring depth per warp
+constexpr int SWEEP_WARPS = 8;
+constexpr int GUARD = 256;    // elements kept readable before and after a population buffer
+constexpr float PHI_CUT_WIDTHS = 4.0f;   // phi tail kept up to 4 interface widths (phi > 1.1e-7)
+constexpr unsigned long long WAIT_LIMIT_NS = 1000000000ull;   // bounded device waits: 1 s
 
 enum : int { SIDE_PERIODIC = 0, SIDE_VELOCITY = 1, SIDE_PRESSURE = 2 };
 enum : int { WEST = 0, EAST = 1, SOUTH = 2, NORTH = 3 };
-enum : int { ERR_UNSTABLE = 1, ERR_OVERFLOW = 2 };
+enum : int { ERR_UNSTABLE = 1, ERR_OVERFLOW = 2, ERR_TIMEOUT = 4 };
 
 // D2Q9 directions of Eq. 3 and weights of Eq. 4.
 __host__ __device__ constexpr int cxof(int i) { return i == 1 || i == 5 || i == 8 ? 1 : (i == 3 || i == 6 || i == 7 ? -1 : 0); }
@@ -44,20 +59,23 @@ template <typename T> struct Storage;
 
 template <> struct Storage<float> {
     static __device__ __forceinline__ float4 load4(const float *p) { return __ldg(reinterpret_cast<const float4 *>(p)); }
+    static __device__ __forceinline__ float4 lds4(const float *p) { return *reinterpret_cast<const float4 *>(p); }
     static __device__ __forceinline__ float load1(const float *p) { return __ldg(p); }
+    static __device__ __forceinline__ float lds1(const float *p) { return *p; }
     static __device__ __forceinline__ void store4(float *p, float4 v) { *reinterpret_cast<float4 *>(p) = v; }
     static __device__ __forceinline__ void store1(float *p, float v) { *p = v; }
-    static __host__ __device__ float from_float(float v) { return v; }
 };
 
 template <> struct Storage<__half> {
-    static __device__ __forceinline__ float4 load4(const __half *p) {
-        uint2 u = __ldg(reinterpret_cast<const uint2 *>(p));
+    static __device__ __forceinline__ float4 cvt(uint2 u) {
         __half2 a = *reinterpret_cast<__half2 *>(&u.x), b = *reinterpret_cast<__half2 *>(&u.y);
         float2 fa = __half22float2(a), fb = __half22float2(b);
         return make_float4(fa.x, fa.y, fb.x, fb.y);
     }
+    static __device__ __forceinline__ float4 load4(const __half *p) { return cvt(__ldg(reinterpret_cast<const uint2 *>(p))); }
+    static __device__ __forceinline__ float4 lds4(const __half *p) { return cvt(*reinterpret_cast<const uint2 *>(p)); }
     static __device__ __forceinline__ float load1(const __half *p) { return __half2float(__ldg(p)); }
+    static __device__ __forceinline__ float lds1(const __half *p) { return __half2float(*p); }
     static __device__ __forceinline__ void store4(__half *p, float4 v) {
         __half2 a = __floats2half2_rn(v.x, v.y), b = __floats2half2_rn(v.z, v.w);
         uint2 u;
@@ -69,13 +87,15 @@ template <> struct Storage<__half> {
 };
 
 template <> struct Storage<__nv_bfloat16> {
-    static __device__ __forceinline__ float4 load4(const __nv_bfloat16 *p) {
-        uint2 u = __ldg(reinterpret_cast<const uint2 *>(p));
+    static __device__ __forceinline__ float4 cvt(uint2 u) {
         __nv_bfloat162 a = *reinterpret_cast<__nv_bfloat162 *>(&u.x), b = *reinterpret_cast<__nv_bfloat162 *>(&u.y);
         float2 fa = __bfloat1622float2(a), fb = __bfloat1622float2(b);
         return make_float4(fa.x, fa.y, fb.x, fb.y);
     }
+    static __device__ __forceinline__ float4 load4(const __nv_bfloat16 *p) { return cvt(__ldg(reinterpret_cast<const uint2 *>(p))); }
+    static __device__ __forceinline__ float4 lds4(const __nv_bfloat16 *p) { return cvt(*reinterpret_cast<const uint2 *>(p)); }
     static __device__ __forceinline__ float load1(const __nv_bfloat16 *p) { return __bfloat162float(__ldg(p)); }
+    static __device__ __forceinline__ float lds1(const __nv_bfloat16 *p) { return __bfloat162float(*p); }
     static __device__ __forceinline__ void store4(__nv_bfloat16 *p, float4 v) {
         __nv_bfloat162 a = __floats2bfloat162_rn(v.x, v.y), b = __floats2bfloat162_rn(v.z, v.w);
         uint2 u;
@@ -86,18 +106,34 @@ template <> struct Storage<__nv_bfloat16> {
     static __device__ __forceinline__ void store1(__nv_bfloat16 *p, float v) { *p = __float2bfloat16_rn(v); }
 };
 
+// Elements in the 16-byte halo on each side of a staged row segment, and the
+// staged width.
+template <typename T> __host__ __device__ constexpr int halo_of() { return 16 / (int)sizeof(T); }
+template <typename T> __host__ __device__ constexpr int segw_of() { return TILE_W + 2 * halo_of<T>(); }
+
+// Dynamic shared memory of one sweep block.
+template <typename T> __host__ __device__ constexpr size_t sweep_smem_bytes() {
+    return (size_t)SWEEP_WARPS * STAGES * 9 * segw_of<T>() * sizeof(T)   // staged rows
+           + (size_t)SWEEP_WARPS * MAXC * NREC * sizeof(float4)           // candidate records
+           + (size_t)SWEEP_WARPS * MAXC * sizeof(int)                     // candidate ids
+           + (size_t)SWEEP_WARPS * STAGES * sizeof(uint64_t);             // mbarriers
+}
+
 // ------------------------------------------------------------ parameters
 struct Particles {      // structure of arrays, device memory
-    double *x, *y, *r, *ux, *uy, *omega, *theta, *rho_s;
-    float *xf, *yf;     // FP32 copy of the centre, for cheap proximity tests
+    double *x[2], *y[2];        // centre, by step parity
+    float *xf[2], *yf[2];       // FP32 copy of the centre, for cheap proximity tests
+    double *r, *ux, *uy, *omega, *theta, *rho_s;
     int *fixed;
 };
 
 struct Lattice {
-    int nx, ny, pitch;          // nodes; row pitch in elements (multiple of 4)
+    int nx, ny, pitch;          // nodes; row pitch in elements (multiple of 32)
     long long plane;            // elements per population plane (ny * pitch)
     int ntx, nty;               // tiles along x and y
     int per_x, per_y;           // periodic axes
+    int wrap_x, wrap_y;         // periodic and short enough that a tile's nodes
+                                // need their own minimum image
     int side_kind[4];
     float side_ux[4], side_uy[4], side_drho[4];   // drho = rho_b - 1
 };
@@ -111,10 +147,13 @@ struct Physics {
     double cut_d;
 };
 
-struct Bins {
+struct Bins {                   // one set per step parity
     int *count;                 // per tile: particles binned (may exceed MAXC)
     int *ids;                   // per tile: MAXC particle ids
-    double *partial;            // per tile and slot: Fx, Fy, T
+    float4 *rec;                // per tile and slot, 3 records: (cx_hi, cx_lo, cy_hi, cy_lo),
+                                // (r, ux_hi, uy_hi, omega_hi), (ux_lo, uy_lo, omega_lo, 0)
+    int *pslot;                 // per particle: MAXT entries tile * MAXC + slot (-1: overflowed)
+    int *npslot;                // per particle: tiles reached
 };
 
 // ------------------------------------------------------------ small helpers
@@ -123,10 +162,76 @@ __device__ __forceinline__ int wrap_or_clamp(int v, int n, int periodic) {
     return v < 0 ? 0 : (v >= n ? n - 1 : v);
 }
 
-// Equilibrium deviation f^eq_i(rho, u) - w_i (Eq. 2) with rho = 1 + drho.
-__device__ __forceinline__ float eq_dev(int i, float drho, float rho, float ux, float uy, float usq) {
-    const float cu = cxof(i) * ux + cyof(i) * uy;
-    return wof(i) * (drho + rho * (3.0f * cu + 4.5f * cu * cu - 1.5f * usq));
+// Populations of the form X_i = w_i [S + 3 c_i.B + 4.5 c_i^T M c_i] (the
+// equilibrium of Eq. 2 has this form with B = rho u, M = rho u u^T; so has the
+// collision's relaxation target plus force term of Eqs. 13 and 15), for a
+// given zeroth moment m0 = sum_i X_i, so S = m0 - 1.5 tr M.
+//
+// The constants are chosen so that the moments come out exact for the FP32
+// constants themselves: 4.5 w_1 = 1/2 and 4.5 w_5 = 1/8 are exact, the
+// first-moment weights a1 ~ 1/3 and a5 = (1 - 2 a1) / 4 satisfy
+// 2 a1 + 4 a5 = 1 exactly, and X_0 takes the remainder of m0.  Rounded
+// weights would otherwise bias the momentum by ~1e-8 every step.
+constexpr float W1F = 1.0f / 9.0f, W5F = 1.0f / 36.0f;
+constexpr float A1F = 1.0f / 3.0f;
+constexpr float A5F = (float)((1.0 - 2.0 * (double)A1F) / 4.0);
+
+__device__ __forceinline__ void moment_form(float m0, float Bx, float By, float Mxx, float Myy, float Mxy, float X[9]) {
+    const float S = m0 - 1.5f * (Mxx + Myy);
+    const float ax = fmaf(W1F, S, 0.5f * Mxx), ay = fmaf(W1F, S, 0.5f * Myy);
+    const float tr = Mxx + Myy;
+    const float ap = fmaf(W5F, S, 0.125f * fmaf(2.0f, Mxy, tr));
+    const float am = fmaf(W5F, S, 0.125f * fmaf(-2.0f, Mxy, tr));
+    const float bx = A1F * Bx, by = A1F * By, bp = A5F * (Bx + By), bm = A5F * (By - Bx);
+    X[0] = m0 - 2.0f * ((ax + ay) + (ap + am));
+    X[1] = ax + bx; X[3] = ax - bx;
+    X[2] = ay + by; X[4] = ay - by;
+    X[5] = ap + bp; X[7] = ap - bp;
+    X[6] = am + bm; X[8] = am - bm;
+}
+
+// Equilibrium deviation f^eq_i(rho, u) - w_i (Eq. 2), rho = 1 + drho.
+__device__ __forceinline__ void eq_dev9(float drho, float rho, float ux, float uy, float X[9]) {
+    const float rux = rho * ux, ruy = rho * uy;
+    moment_form(drho, rux, ruy, rux * ux, ruy * uy, rux * uy, X);
+}
+
+// Collision of Eq. 13 with f^eq of Eq. 2 (corrected velocity, Eq. 17) and the
+// force term of Eq. 15, in deviation form:
+//   d'_i = d_i + (X_i - omega d_i),  X_i = omega d^eq_i + phi F_i,
+// and X has the form w_i [S + 3 c_i.B + 4.5 c_i^T M c_i] with
+//   B = omega rho u + k (u_s - u*),  M = omega rho u u^T + k (u_s u_s^T - u* u*^T),
+//   sum_i X_i = omega (rho - 1),     k = (1 - 1/2tau) rho phi,
+// which is Eqs. 2 and 15 summed and regrouped by powers of c_i.  Because
+// rho u = j + phi rho (u_s - u*) / 2 (Eq. 17) and omega/2 + (1 - 1/2tau) = 1,
+// B = omega j + phi rho (u_s - u*): the momentum handed to the fluid is formed
+// without dividing by rho, so no rounding of j / rho biases it.  The force
+// part of M is formed from (u_s - u*) and (u_s + u*) rather than as a
+// difference of squares.
+__device__ __forceinline__ void collide(float d[9], float omega, float drho, float rho, float jx, float jy,
+                                        float ux, float uy, float kphi, float prho, float dux, float duy,
+                                        float usx, float usy, float uax, float uay) {
+    const float orho = omega * rho;
+    const float Bx = fmaf(omega, jx, prho * dux), By = fmaf(omega, jy, prho * duy);
+    const float Mxx = fmaf(orho * ux, ux, kphi * (dux * (usx + uax)));
+    const float Myy = fmaf(orho * uy, uy, kphi * (duy * (usy + uay)));
+    const float Mxy = fmaf(orho * ux, uy, kphi * fmaf(dux, usy, uax * duy));
+    float X[9];
+    moment_form(omega * drho, Bx, By, Mxx, Myy, Mxy, X);
+#pragma unroll
+    for (int i = 0; i < 9; ++i) d[i] += fmaf(-omega, d[i], X[i]);
+}
+
+// The same collision with phi = 0 (plain BGK of Eq. 1): X_i = omega d^eq_i,
+// B = omega j.
+__device__ __forceinline__ void collide_plain(float d[9], float omega, float drho, float rho, float jx, float jy,
+                                              float ux, float uy) {
+    const float orho = omega * rho;
+    const float Bx = omega * jx, By = omega * jy;
+    float X[9];
+    moment_form(omega * drho, Bx, By, orho * ux * ux, orho * uy * uy, orho * ux * uy, X);
+#pragma unroll
+    for (int i = 0; i < 9; ++i) d[i] += fmaf(-omega, d[i], X[i]);
 }
 
 // Tile ranges along one axis covered by [X - R, X + R] (a disc's bounding
@@ -156,14 +261,78 @@ __host__ __device__ inline AxisTiles axis_tiles(double X, double R, int n, int t
     return t;
 }
 
-// ------------------------------------------------------------ the sweep
-// Mode: STEP writes the collided populations and the force partials; FIELDS
-// writes rho, the corrected velocity and phi of the streamed state instead.
-enum : int { MODE_STEP = 0, MODE_FIELDS = 1 };
+// ------------------------------------------------------------ async copies
+__device__ __forceinline__ uint32_t smem_u32(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
 
-struct FieldsOut {
-    float *rho, *ux, *uy, *phi;   // dense [ny][nx]
-};
+__device__ __forceinline__ void mbar_init(uint64_t *bar, uint32_t count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+}
+
+__device__ __forceinline__ void mbar_fence_init() {
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+
+__device__ __forceinline__ void mbar_expect_tx(uint64_t *bar, uint32_t bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes) : "memory");
+}
+
+__device__ __forceinline__ bool mbar_try_wait(uint64_t *bar, uint32_t parity) {
+    uint32_t ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(ok)
+        : "r"(smem_u32(bar)), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+
+__device__ __forceinline__ unsigned long long global_ns() {
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
+// Wait for a phase of an mbarrier, giving up after WAIT_LIMIT_NS.
+__device__ __forceinline__ bool mbar_wait_bounded(uint64_t *bar, uint32_t parity) {
+    if (mbar_try_wait(bar, parity)) return true;
+    const unsigned long long t0 = global_ns();
+    for (;;) {
+        if (mbar_try_wait(bar, parity)) return true;
+        if (global_ns() - t0 > WAIT_LIMIT_NS) return false;
+    }
+}
+
+// Order this thread's earlier shared-memory reads before later writes of the
+// async proxy (the bulk copies) to the same buffer.
+__device__ __forceinline__ void fence_proxy_async_smem() {
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+}
+
+__device__ __forceinline__ void bulk_copy_g2s(void *dst, const void *src, uint32_t bytes, uint64_t *bar) {
+    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];"
+                 ::"r"(smem_u32(dst)), "l"(src), "r"(bytes), "r"(smem_u32(bar))
+                 : "memory");
+}
+
+// Stage the nine source rows of row segment (row y, segment tx):
+// plane i comes from row y - c_iy, columns [tx*128 - halo, tx*128 + 128 + halo).
+// Lane 0 arms the barrier with the byte count, lanes 0..8 issue one copy each.
+// The population buffers carry GUARD readable elements before and after, so
+// the copies of edge segments stay inside the allocation.
+template <typename T>
+__device__ __forceinline__ void issue_segment(const T *__restrict__ src, const Lattice &L, int y, int tx, T *stage,
+                                              uint64_t *bar, int lane) {
+    constexpr int H = halo_of<T>(), SW = segw_of<T>();
+    if (lane == 0) mbar_expect_tx(bar, 9u * SW * sizeof(T));
+    __syncwarp();
+    if (lane < 9) {
+        const int sy = wrap_or_clamp(y - cyof(lane), L.ny, L.per_y);
+        const T *g = src + lane * L.plane + (long long)sy * L.pitch + (tx * TILE_W - H);
+        bulk_copy_g2s(stage + lane * SW, g, SW * sizeof(T), bar);
+    }
+}
 
 template <typename T>
 __device__ __forceinline__ void pull_node_scalar(const T *__restrict__ src, const Lattice &L, int x, int y, float d[9]) {
@@ -209,250 +378,307 @@ __device__ __forceinline__ void edge_extrapolate(const T *__restrict__ src, cons
     } else {
         drb = sdr; ubx = unx; uby = uny;
     }
-    const float rhob = 1.0f + drb;
-    const float usqb = ubx * ubx + uby * uby, usqn = unx * unx + uny * uny;
+    float eb[9], en[9];
+    eq_dev9(drb, 1.0f + drb, ubx, uby, eb);
+    eq_dev9(drn, rhon, unx, uny, en);
 #pragma unroll
-    for (int i = 0; i < 9; ++i)
-        d[i] = eq_dev(i, drb, rhob, ubx, uby, usqb) + (dn[i] - eq_dev(i, drn, rhon, unx, uny, usqn));
+    for (int i = 0; i < 9; ++i) d[i] = eb[i] + (dn[i] - en[i]);
 }
 
-template <typename T, int MODE>
-__global__ void __launch_bounds__(256)
+// ------------------------------------------------------------ the sweep
+// Mode: STEP writes the collided populations and the force partials; FIELDS
+// writes rho, the corrected velocity and phi of the streamed state instead.
+enum : int { MODE_STEP = 0, MODE_FIELDS = 1 };
+
+struct FieldsOut {
+    float *rho, *ux, *uy, *phi;   // dense [ny][nx]
+};
+
+template <typename T, int MODE, bool EDGES>
+__global__ void __launch_bounds__(SWEEP_WARPS * 32, 2)
 sweep_kernel(const T *__restrict__ src, T *__restrict__ dst, Lattice L, Physics ph,
-             Particles P, Bins B, FieldsOut fo, int *__restrict__ err)
+             Bins B, float4 *__restrict__ partial, int *__restrict__ clear_count, FieldsOut fo,
+             int *__restrict__ err)
 {
-    __shared__ int s_n;
-    __shared__ int s_id[MAXC];
-    __shared__ float s_cxh[MAXC], s_cxl[MAXC], s_cyh[MAXC], s_cyl[MAXC];
-    __shared__ float s_r[MAXC], s_ux[MAXC], s_uy[MAXC], s_om[MAXC];
-    __shared__ float s_red[TILE_H][MAXC][3];
+    constexpr int H = halo_of<T>(), SW = segw_of<T>();
+    constexpr size_t STAGE_BYTES = (size_t)SWEEP_WARPS * STAGES * 9 * SW * sizeof(T);
+    constexpr size_t REC_BYTES = (size_t)SWEEP_WARPS * NREC * MAXC * sizeof(float4);
+    constexpr size_t ID_BYTES = (size_t)SWEEP_WARPS * MAXC * sizeof(int);
+    extern __shared__ __align__(128) unsigned char smem_raw[];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    T *const stages = reinterpret_cast<T *>(smem_raw) + (size_t)warp * STAGES * 9 * SW;
+    float4 *const crec = reinterpret_cast<float4 *>(smem_raw + STAGE_BYTES) + (size_t)warp * NREC * MAXC;
+    int *const cid = reinterpret_cast<int *>(smem_raw + STAGE_BYTES + REC_BYTES) + warp * MAXC;
+    uint64_t *const bars = reinterpret_cast<uint64_t *>(smem_raw + STAGE_BYTES + REC_BYTES + ID_BYTES) + warp * STAGES;
 
-    const int lane = threadIdx.x, wy = threadIdx.y;
-    const int tx = blockIdx.x, ty = blockIdx.y;
-    const int tile = ty * L.ntx + tx;
-    const int tx0 = tx * TILE_W, ty0 = ty * TILE_H;
-    const int tid = wy * 32 + lane;
-
-    // Candidate particles of this tile: centre relative to the tile origin,
-    // minimum image about the tile centre, as an FP32 hi + lo pair.
-    if (tid == 0) {
-        int n = B.count ? B.count[tile] : 0;
-        s_n = n > MAXC ? MAXC : n;
+    if (lane == 0) {
+        for (int s = 0; s < STAGES; ++s) mbar_init(&bars[s], 1);
+        mbar_fence_init();
     }
-    __syncthreads();
-    const int ncand = s_n;
-    if (tid < ncand) {
-        const int q = B.ids[tile * MAXC + tid];
-        double cx = P.x[q] - (double)tx0, cy = P.y[q] - (double)ty0;
-        if (L.per_x) {
-            const double h = 0.5 * TILE_W;
-            while (cx - h >= 0.5 * L.nx) cx -= L.nx;
-            while (cx - h < -0.5 * L.nx) cx += L.nx;
-        }
-        if (L.per_y) {
-            const double h = 0.5 * TILE_H;
-            while (cy - h >= 0.5 * L.ny) cy -= L.ny;
-            while (cy - h < -0.5 * L.ny) cy += L.ny;
-        }
-        const float cxh = (float)cx, cyh = (float)cy;
-        s_id[tid] = q;
-        s_cxh[tid] = cxh; s_cxl[tid] = (float)(cx - (double)cxh);
-        s_cyh[tid] = cyh; s_cyl[tid] = (float)(cy - (double)cyh);
-        s_r[tid] = (float)P.r[q];
-        s_ux[tid] = (float)P.ux[q];
-        s_uy[tid] = (float)P.uy[q];
-        s_om[tid] = (float)P.omega[q];
-    }
-    __syncthreads();
+    __syncwarp();
+    // the next step's bins start empty (nothing reads them during this sweep)
+    if (clear_count)
+        for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < L.ntx * L.nty; t += gridDim.x * blockDim.x)
+            clear_count[t] = 0;
 
-    const int y = ty0 + wy;
-    const int x0 = tx0 + lane * VEC;
-    const bool row_ok = y < L.ny;
-    const int yc = row_ok ? y : L.ny - 1;               // rows past the end read a valid row
-    const int xl = x0 <= L.pitch - VEC ? x0 : L.pitch - VEC;
-
-    // ---- pull-stream: f_i(x, t+1) = f'_i(x - c_i, t), 4 nodes per thread
-    float d[9][VEC];
-#pragma unroll
-    for (int i = 0; i < 9; ++i) {
-        const int cx = cxof(i), cy = cyof(i);
-        const int sy = wrap_or_clamp(yc - cy, L.ny, L.per_y);
-        const T *row = src + i * L.plane + (long long)sy * L.pitch;
-        const float4 v = Storage<T>::load4(row + xl);
-        if (cx == 0) {
-            d[i][0] = v.x; d[i][1] = v.y; d[i][2] = v.z; d[i][3] = v.w;
-        } else if (cx == 1) {
-            float left = __shfl_up_sync(0xffffffffu, v.w, 1);
-            if (lane == 0) left = Storage<T>::load1(row + wrap_or_clamp(x0 - 1, L.nx, L.per_x));
-            d[i][0] = left; d[i][1] = v.x; d[i][2] = v.y; d[i][3] = v.z;
-        } else {
-            float right = __shfl_down_sync(0xffffffffu, v.x, 1);
-            if (lane == 31 || x0 + VEC >= L.nx) {
-                // lanes past the row end may sit more than one period beyond it
-                const int xr = x0 + VEC;
-                right = Storage<T>::load1(row + (L.per_x ? xr % L.nx : (xr < L.nx ? xr : L.nx - 1)));
-            }
-            d[i][0] = v.y; d[i][1] = v.z; d[i][2] = v.w; d[i][3] = right;
-            // the row's last node when nx is not a multiple of 4: its right
-            // neighbour wraps to column 0, not the padding in this vector
-            const int kl = L.nx - 1 - x0;
-            if (kl >= 0 && kl < VEC - 1) {
-                const float wv = Storage<T>::load1(row + wrap_or_clamp(L.nx, L.nx, L.per_x));
-#pragma unroll
-                for (int k = 0; k < VEC - 1; ++k)
-                    if (k == kl) d[i][k] = wv;
-            }
+    const int nitems = L.ny * L.ntx;
+    const int gw = blockIdx.x * SWEEP_WARPS + warp, nw = gridDim.x * SWEEP_WARPS;
+    // item = y * ntx + tx, advanced by nw per iteration without dividing
+    const int dy_step = nw / L.ntx, dtx_step = nw - dy_step * L.ntx;
+    auto advance = [&](int &yy, int &xx) {
+        xx += dtx_step;
+        yy += dy_step;
+        if (xx >= L.ntx) { xx -= L.ntx; ++yy; }
+    };
+    int y = gw / L.ntx, tx = gw - (gw / L.ntx) * L.ntx;
+    {
+        int py = y, ptx = tx;
+        for (int s = 0; s < STAGES; ++s) {
+            if (gw + s * nw < nitems) issue_segment<T>(src, L, py, ptx, stages + s * 9 * SW, &bars[s], lane);
+            advance(py, ptx);
         }
     }
 
-    const bool edge_tile = (!L.per_x && (tx0 == 0 || tx0 + TILE_W >= L.nx)) ||
-                           (!L.per_y && (ty0 == 0 || ty0 + TILE_H >= L.ny));
+    uint32_t parity = 0;     // bit s: phase parity the next wait on stage s expects
+    uint32_t pending = 0;    // bit s: stage s has copies in flight
+    for (int s = 0; s < STAGES; ++s)
+        if (gw + s * nw < nitems) pending |= 1u << s;
+    bool bad = false, timed_out = false;
+    int k = 0;
+    for (int item = gw; item < nitems; item += nw, ++k) {
+        if (k > 0) advance(y, tx);
+        const int s = k % STAGES;
+        const int ty = y / TILE_H, tile = ty * L.ntx + tx;
+        const int tx0 = tx * TILE_W, ty0 = ty * TILE_H;
+        const int x0 = tx0 + lane * VEC;
 
-    float acc[VEC][3];     // per-node force / torque contribution
-    int own[VEC];          // owning slot per node, -1 if none
-    bool bad = false;
-
+        // ---- the tile's candidate particles (records written by the binning)
+        __syncwarp();
+        int ncand = B.count ? B.count[tile] : 0;
+        ncand = ncand > MAXC ? MAXC : ncand;
+        if (lane < ncand) {
+            const long long r = (long long)tile * MAXC + lane;
 #pragma unroll
-    for (int k = 0; k < VEC; ++k) {
-        const int x = x0 + k;
-        const bool active = row_ok && x < L.nx;
-        own[k] = -1;
-        acc[k][0] = acc[k][1] = acc[k][2] = 0.f;
-        float dk[9];
-#pragma unroll
-        for (int i = 0; i < 9; ++i) dk[i] = d[i][k];
-        if (edge_tile && active) {
-            const bool onx = !L.per_x && (x == 0 || x == L.nx - 1);
-            const bool ony = !L.per_y && (y == 0 || y == L.ny - 1);
-            if (onx || ony) edge_extrapolate<T>(src, L, x, y, dk);
+            for (int q = 0; q < NREC; ++q) crec[q * MAXC + lane] = B.rec[NREC * r + q];
+            cid[lane] = B.ids[r];
         }
 
-        // ---- moments (Eq. 5, Eq. 16)
-        const float drho = ((dk[0] + dk[1]) + (dk[2] + dk[3])) + ((dk[4] + dk[5]) + (dk[6] + dk[7])) + dk[8];
-        const float rho = 1.0f + drho;
-        const float jx = (dk[1] - dk[3]) + (dk[5] - dk[6]) + (dk[8] - dk[7]);
-        const float jy = (dk[2] - dk[4]) + (dk[5] + dk[6]) - (dk[7] + dk[8]);
-        const float uax = jx / rho, uay = jy / rho;
-
-        // ---- solid fraction (Eq. 14) from the tile's candidates: max rule
-        float phi = 0.f, usx = 0.f, usy = 0.f, rx = 0.f, ry = 0.f;
-        int best = -1, best_id = 0x7fffffff;
-        for (int c = 0; c < ncand; ++c) {
-            float dx = ((float)(x - tx0) - s_cxh[c]) - s_cxl[c];
-            float dy = ((float)(y - ty0) - s_cyh[c]) - s_cyl[c];
-            if (L.per_x) { if (dx >= 0.5f * L.nx) dx -= L.nx; else if (dx < -0.5f * L.nx) dx += L.nx; }
-            if (L.per_y) { if (dy >= 0.5f * L.ny) dy -= L.ny; else if (dy < -0.5f * L.ny) dy += L.ny; }
-            const float rr = s_r[c] + ph.cut;
-            const float d2 = dx * dx + dy * dy;
-            if (d2 > rr * rr) continue;
-            const float l = s_r[c] - sqrtf(d2);
-            if (l < -ph.cut) continue;
-            // (1 + tanh(2l/eps)) / 2 == 1 / (1 + exp(-4l/eps))
-            const float pc = 1.0f / (1.0f + expf(-ph.four_over_eps * l));
-            const int id = s_id[c];
-            if (pc > phi || (pc == phi && pc > 0.f && id < best_id)) {
-                phi = pc; best = c; best_id = id; rx = dx; ry = dy;
-            }
-        }
-        if (best >= 0) {
-            usx = s_ux[best] - s_om[best] * ry;   // u_s = U + omega x r
-            usy = s_uy[best] + s_om[best] * rx;
-        }
-
-        // ---- corrected velocity (Eq. 17)
-        const float hx = 0.5f * phi * (usx - uax), hy = 0.5f * phi * (usy - uay);
-        const float ux = uax + hx, uy = uay + hy;
-
-        if (MODE == MODE_FIELDS) {
-            if (active) {
-                const long long o = (long long)y * L.nx + x;
-                if (fo.rho) fo.rho[o] = rho;
-                if (fo.ux) fo.ux[o] = ux;
-                if (fo.uy) fo.uy[o] = uy;
-                if (fo.phi) fo.phi[o] = phi;
-            }
-            continue;
-        }
-
-        if (active && (!(rho > 0.0f) || !isfinite(uax + uay))) bad = true;
-
-        // ---- collision with the force term (Eqs. 2, 13, 15)
-        const float usq = ux * ux + uy * uy;
-        if (best >= 0) {
-            const float dux = usx - uax, duy = usy - uay;
-            const float ssq = (usx * usx + usy * usy) - (uax * uax + uay * uay);
-            const float kr = ph.kf * rho * phi;
-#pragma unroll
-            for (int i = 0; i < 9; ++i) {
-                const float cx = (float)cxof(i), cy = (float)cyof(i);
-                const float cus = cx * usx + cy * usy, cua = cx * uax + cy * uay;
-                const float Fi = wof(i) * (3.0f * (cx * dux + cy * duy) + 4.5f * (cus * cus - cua * cua) - 1.5f * ssq);
-                const float deq = eq_dev(i, drho, rho, ux, uy, usq);
-                dk[i] = dk[i] - ph.omega * (dk[i] - deq) + kr * Fi;
-            }
-            // Eqs. 18-19 per node, by the closed form sum_i F_i c_i = kf rho (u_s - u*)
-            if (active) {
-                const float s = -phi * ph.kforce * rho;
-                const float gx = s * dux, gy = s * duy;
-                own[k] = best;
-                acc[k][0] = gx; acc[k][1] = gy; acc[k][2] = rx * gy - ry * gx;
-            }
-        } else {
-#pragma unroll
-            for (int i = 0; i < 9; ++i) {
-                const float deq = eq_dev(i, drho, rho, ux, uy, usq);
-                dk[i] = dk[i] - ph.omega * (dk[i] - deq);
-            }
-        }
-#pragma unroll
-        for (int i = 0; i < 9; ++i) d[i][k] = dk[i];
-    }
-
-    if (MODE == MODE_FIELDS) return;
-
-    if (bad) atomicOr(err, ERR_UNSTABLE);
-
-    // ---- store the collided populations
-    if (row_ok) {
-        const bool full = x0 + VEC <= L.nx;
+        // ---- pull-stream from the staged rows: f_i(x, t+1) = f'_i(x - c_i, t)
+        // a warp-uniform decision: every lane leaves together if any gave up
+        if (!__all_sync(0xffffffffu, mbar_wait_bounded(&bars[s], (parity >> s) & 1u))) { timed_out = true; break; }
+        parity ^= 1u << s;
+        pending &= ~(1u << s);
+        const T *st = stages + s * 9 * SW;
+        const int c0 = H + lane * VEC;
+        float d[9][VEC];
 #pragma unroll
         for (int i = 0; i < 9; ++i) {
-            T *row = dst + i * L.plane + (long long)y * L.pitch;
-            if (full) {
-                Storage<T>::store4(row + x0, make_float4(d[i][0], d[i][1], d[i][2], d[i][3]));
+            const float4 v = Storage<T>::lds4(st + i * SW + c0);
+            if (cxof(i) == 0) {
+                d[i][0] = v.x; d[i][1] = v.y; d[i][2] = v.z; d[i][3] = v.w;
+            } else if (cxof(i) == 1) {
+                d[i][0] = Storage<T>::lds1(st + i * SW + c0 - 1); d[i][1] = v.x; d[i][2] = v.y; d[i][3] = v.z;
             } else {
-#pragma unroll
-                for (int k = 0; k < VEC; ++k)
-                    if (x0 + k < L.nx) Storage<T>::store1(row + x0 + k, d[i][k]);
+                d[i][0] = v.y; d[i][1] = v.z; d[i][2] = v.w; d[i][3] = Storage<T>::lds1(st + i * SW + c0 + VEC);
             }
+        }
+        __syncwarp();
+        // recycle the stage for the segment STAGES items ahead
+        {
+            const int nxt = item + STAGES * nw;
+            if (nxt < nitems) {
+                int ny2 = y, nx2 = tx;
+                for (int q = 0; q < STAGES; ++q) advance(ny2, nx2);
+                fence_proxy_async_smem();
+                issue_segment<T>(src, L, ny2, nx2, stages + s * 9 * SW, &bars[s], lane);
+                pending |= 1u << s;
+            }
+        }
+        // periodic x: the row's first node pulls from column nx-1 and its
+        // last node from column 0, which the staged halo does not hold
+        if (L.per_x && (tx == 0 || tx0 + TILE_W >= L.nx)) {
+#pragma unroll
+            for (int i = 0; i < 9; ++i) {
+                if (cxof(i) == 0) continue;
+                const int sy = wrap_or_clamp(y - cyof(i), L.ny, L.per_y);
+                const T *row = src + i * L.plane + (long long)sy * L.pitch;
+                if (cxof(i) == 1 && x0 == 0) d[i][0] = Storage<T>::load1(row + (L.nx - 1));
+                if (cxof(i) == -1) {
+                    const int kl = L.nx - 1 - x0;
+#pragma unroll
+                    for (int q = 0; q < VEC; ++q)
+                        if (q == kl) d[i][q] = Storage<T>::load1(row);
+                }
+            }
+        }
+        __syncwarp();   // candidate records visible to the whole warp
+
+        // ---- solid fraction (Eq. 14), owner and particle velocity per node:
+        // max over the tile's candidates, lowest particle id on ties
+        float phi[VEC], rxn[VEC], ryn[VEC];
+        int best[VEC], best_id[VEC];
+#pragma unroll
+        for (int q = 0; q < VEC; ++q) { phi[q] = 0.f; rxn[q] = 0.f; ryn[q] = 0.f; best[q] = -1; best_id[q] = 0x7fffffff; }
+        for (int c = 0; c < ncand; ++c) {
+            const float4 ra = crec[c], rb = crec[MAXC + c];
+            const float R = rb.x + ph.cut;
+            float dy = ((float)(y - ty0) - ra.z) - ra.w;
+            if (L.wrap_y) { if (dy >= 0.5f * L.ny) dy -= L.ny; else if (dy < -0.5f * L.ny) dy += L.ny; }
+            const float h2 = R * R - dy * dy;
+            if (h2 < 0.f) continue;                         // this row misses the disc tail
+            const float dx0 = ((float)(x0 - tx0) - ra.x) - ra.y;
+            if (!L.wrap_x) {
+                // the thread's 4 nodes span [dx0, dx0 + 3]
+                const float lo = dx0 > 0.f ? dx0 : (dx0 + (VEC - 1) < 0.f ? -(dx0 + (VEC - 1)) : 0.f);
+                if (lo * lo > h2) continue;
+            }
+            const int id = cid[c];
+#pragma unroll
+            for (int q = 0; q < VEC; ++q) {
+                float dx = dx0 + (float)q;
+                if (L.wrap_x) { if (dx >= 0.5f * L.nx) dx -= L.nx; else if (dx < -0.5f * L.nx) dx += L.nx; }
+                const float d2 = dx * dx + dy * dy;
+                if (d2 > R * R) continue;
+                const float l = rb.x - sqrtf(d2);
+                if (l < -ph.cut) continue;
+                // (1 + tanh(2l/eps)) / 2 == 1 / (1 + exp(-4l/eps))
+                const float pc = 1.0f / (1.0f + expf(-ph.four_over_eps * l));
+                if (pc > phi[q] || (pc == phi[q] && pc > 0.f && id < best_id[q])) {
+                    phi[q] = pc; best[q] = c; best_id[q] = id; rxn[q] = dx; ryn[q] = dy;
+                }
+            }
+        }
+
+        const bool row_edge = EDGES && !L.per_y && (y == 0 || y == L.ny - 1);
+        const bool col_edge = EDGES && !L.per_x && (tx == 0 || tx0 + TILE_W >= L.nx);
+        // warps with no node inside any particle's phi tail collide without the force term
+        const bool coupled = __any_sync(0xffffffffu, max(max(best[0], best[1]), max(best[2], best[3])) >= 0);
+        float acc[VEC][3];
+
+#pragma unroll
+        for (int q = 0; q < VEC; ++q) {
+            const int x = x0 + q;
+            const bool active = x < L.nx;
+            acc[q][0] = acc[q][1] = acc[q][2] = 0.f;
+            float dk[9];
+#pragma unroll
+            for (int i = 0; i < 9; ++i) dk[i] = d[i][q];
+            if (EDGES && (row_edge || col_edge) && active) {
+                const bool onx = !L.per_x && (x == 0 || x == L.nx - 1);
+                if (row_edge || onx) edge_extrapolate<T>(src, L, x, y, dk);
+            }
+
+            // ---- moments (Eq. 5, Eq. 16)
+            const float drho = ((dk[0] + dk[1]) + (dk[2] + dk[3])) + ((dk[4] + dk[5]) + (dk[6] + dk[7])) + dk[8];
+            const float rho = 1.0f + drho;
+            const float jx = (dk[1] - dk[3]) + (dk[5] - dk[6]) + (dk[8] - dk[7]);
+            const float jy = (dk[2] - dk[4]) + (dk[5] + dk[6]) - (dk[7] + dk[8]);
+            const float inv = 1.0f / rho;
+            const float uax = jx * inv, uay = jy * inv;
+            if (MODE == MODE_STEP && active && (!(rho > 0.0f) || !isfinite(uax + uay))) bad = true;
+
+            if (!coupled) {
+                if (MODE == MODE_FIELDS) {
+                    if (active) {
+                        const long long o = (long long)y * L.nx + x;
+                        if (fo.rho) fo.rho[o] = rho;
+                        if (fo.ux) fo.ux[o] = uax;
+                        if (fo.uy) fo.uy[o] = uay;
+                        if (fo.phi) fo.phi[o] = 0.f;
+                    }
+                    continue;
+                }
+                collide_plain(dk, ph.omega, drho, rho, jx, jy, uax, uay);
+            } else {
+                // u_s - u* from the particle velocity carried as FP32 hi + lo:
+                // u_s = U + omega x r with r the node's offset from the centre
+                float dux = 0.f, duy = 0.f;
+                const int b = best[q];
+                if (b >= 0) {
+                    const float4 rb = crec[MAXC + b], rl = crec[2 * MAXC + b];
+                    dux = fmaf(-rb.w, ryn[q], rb.y - uax) + fmaf(-rl.z, ryn[q], rl.x);
+                    duy = fmaf(rb.w, rxn[q], rb.z - uay) + fmaf(rl.z, rxn[q], rl.y);
+                }
+                const float usx = uax + dux, usy = uay + duy;
+                const float ph_q = phi[q];
+                // ---- corrected velocity (Eq. 17)
+                const float ux = fmaf(0.5f * ph_q, dux, uax), uy = fmaf(0.5f * ph_q, duy, uay);
+
+                if (MODE == MODE_FIELDS) {
+                    if (active) {
+                        const long long o = (long long)y * L.nx + x;
+                        if (fo.rho) fo.rho[o] = rho;
+                        if (fo.ux) fo.ux[o] = ux;
+                        if (fo.uy) fo.uy[o] = uy;
+                        if (fo.phi) fo.phi[o] = ph_q;
+                    }
+                    continue;
+                }
+                collide(dk, ph.omega, drho, rho, jx, jy, ux, uy, ph.kf * rho * ph_q, rho * ph_q, dux, duy, usx, usy,
+                        uax, uay);
+
+                // ---- Eqs. 18-19 per node, by the closed form sum_i F_i c_i = kf rho (u_s - u*)
+                if (active && b >= 0) {
+                    const float sg = -ph_q * ph.kforce * rho;
+                    const float gx = sg * dux, gy = sg * duy;
+                    acc[q][0] = gx; acc[q][1] = gy; acc[q][2] = rxn[q] * gy - ryn[q] * gx;
+                }
+            }
+#pragma unroll
+            for (int i = 0; i < 9; ++i) d[i][q] = dk[i];
+        }
+
+        if (MODE == MODE_FIELDS) continue;
+
+        // ---- store the collided populations
+        {
+            const bool full = x0 + VEC <= L.nx;
+#pragma unroll
+            for (int i = 0; i < 9; ++i) {
+                T *row = dst + i * L.plane + (long long)y * L.pitch;
+                if (full) {
+                    Storage<T>::store4(row + x0, make_float4(d[i][0], d[i][1], d[i][2], d[i][3]));
+                } else {
+#pragma unroll
+                    for (int q = 0; q < VEC; ++q)
+                        if (x0 + q < L.nx) Storage<T>::store1(row + x0 + q, d[i][q]);
+                }
+            }
+        }
+
+        // ---- this row segment's force / torque per candidate (fixed shuffle tree)
+        for (int c = 0; c < ncand; ++c) {
+            if (!coupled) {
+                if (lane == 0)
+                    partial[((long long)tile * MAXC + c) * TILE_H + (y - ty0)] = make_float4(0.f, 0.f, 0.f, 0.f);
+                continue;
+            }
+            float v0 = 0.f, v1 = 0.f, v2 = 0.f;
+#pragma unroll
+            for (int q = 0; q < VEC; ++q)
+                if (best[q] == c) { v0 += acc[q][0]; v1 += acc[q][1]; v2 += acc[q][2]; }
+            if (__any_sync(0xffffffffu, v0 != 0.f || v1 != 0.f || v2 != 0.f)) {
+#pragma unroll
+                for (int o = 16; o > 0; o >>= 1) {
+                    v0 += __shfl_xor_sync(0xffffffffu, v0, o);
+                    v1 += __shfl_xor_sync(0xffffffffu, v1, o);
+                    v2 += __shfl_xor_sync(0xffffffffu, v2, o);
+                }
+            }
+            if (lane == 0)
+                partial[((long long)tile * MAXC + c) * TILE_H + (y - ty0)] = make_float4(v0, v1, v2, 0.f);
         }
     }
 
-    // ---- per-tile, per-candidate force / torque partials (FP64 across warps)
-    if (ncand == 0) return;
-    for (int c = 0; c < ncand; ++c) {
-        float v0 = 0.f, v1 = 0.f, v2 = 0.f;
-#pragma unroll
-        for (int k = 0; k < VEC; ++k)
-            if (own[k] == c) { v0 += acc[k][0]; v1 += acc[k][1]; v2 += acc[k][2]; }
-        if (__any_sync(0xffffffffu, v0 != 0.f || v1 != 0.f || v2 != 0.f)) {
-#pragma unroll
-            for (int o = 16; o > 0; o >>= 1) {
-                v0 += __shfl_xor_sync(0xffffffffu, v0, o);
-                v1 += __shfl_xor_sync(0xffffffffu, v1, o);
-                v2 += __shfl_xor_sync(0xffffffffu, v2, o);
-            }
-        }
-        if (lane == 0) { s_red[wy][c][0] = v0; s_red[wy][c][1] = v1; s_red[wy][c][2] = v2; }
+    if (timed_out) {
+        if (lane == 0) atomicOr(err, ERR_TIMEOUT);
+        // let the copies this warp still has in flight land before the block
+        // releases its shared memory (each wait bounded again)
+        for (int s = 0; s < STAGES; ++s)
+            if (pending & (1u << s)) mbar_wait_bounded(&bars[s], (parity >> s) & 1u);
+        return;
     }
-    __syncthreads();
-    if (tid < ncand * 3) {
-        const int c = tid / 3, comp = tid % 3;
-        double s = 0.0;
-#pragma unroll
-        for (int w = 0; w < TILE_H; ++w) s += (double)s_red[w][c][comp];
-        B.partial[((long long)tile * MAXC + c) * 3 + comp] = s;
-    }
+    if (MODE == MODE_STEP && __any_sync(0xffffffffu, bad) && lane == 0) atomicOr(err, ERR_UNSTABLE);
 }
 
 // ------------------------------------------------------------ particles
@@ -462,65 +688,122 @@ struct BodyParams {
     double eps_p, eps_p2, eps_w, eps_w2, xi;
 };
 
-// One warp per particle: fixed-order FP64 sum of the particle's tile partials
-// (Eqs. 18-19), then the Wan-Turek force (Eqs. 28-29) from the other
-// particles (lanes stride over them) and from the walls.
-__global__ void reduce_kernel(Lattice L, Physics ph, Particles P, Bins B, BodyParams bp,
-                              double *__restrict__ force, double *__restrict__ fcol)
+// Map k in [0, total) of a tile-range set to its tile index, ranges in order.
+__device__ __forceinline__ int range_at(const AxisTiles &a, int k) {
+    const int n0 = a.hi[0] - a.lo[0] + 1;
+    return k < n0 ? a.lo[0] + k : a.lo[1] + (k - n0);
+}
+
+__device__ __forceinline__ int range_len(const AxisTiles &a) {
+    int n = 0;
+    for (int r = 0; r < a.n; ++r) n += a.hi[r] - a.lo[r] + 1;
+    return n;
+}
+
+// One warp per particle.  With integrate != 0:
+//   1. hydrodynamic force and torque (Eqs. 18-19): the row-segment partials of
+//      the tiles the particle was binned into, summed in FP64 in a fixed
+//      order (lanes take fixed (tile, row) entries, then a fixed shuffle tree);
+//   2. Wan-Turek repulsion (Eqs. 28-29) from the other particles (lanes stride
+//      over them) and from mirror images across the walls;
+//   3. symplectic Euler of Eqs. 22-24 (dt = 1), positions read from copy
+//      `pin` and written to copy `pout`.
+// Always, finally: binning of the particle into every tile its phi tail
+// reaches (lanes take the tiles in a fixed order), with the record the sweep
+// reads: the centre relative to the tile origin (minimum image about the tile
+// centre) as FP32 hi + lo, radius and velocities.
+__global__ void particles_kernel(Lattice L, Physics ph, Particles P, BodyParams bp, Bins bin_in, Bins bin_out,
+                                 const float4 *__restrict__ partial, int pin, int pout, int integrate,
+                                 double *__restrict__ force, double *__restrict__ fcol, int *__restrict__ err)
 {
     const int lane = threadIdx.x & 31;
     const int p = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     if (p >= bp.np) return;
-    const double X = P.x[p], Y = P.y[p], r = P.r[p];
+    // pick the position copies without indexing the parameter arrays
+    const double *xin = pin ? P.x[1] : P.x[0], *yin = pin ? P.y[1] : P.y[0];
+    const float *xfin = pin ? P.xf[1] : P.xf[0], *yfin = pin ? P.yf[1] : P.yf[0];
+    double *xout = pout ? P.x[1] : P.x[0], *yout = pout ? P.y[1] : P.y[0];
+    float *xfout = pout ? P.xf[1] : P.xf[0], *yfout = pout ? P.yf[1] : P.yf[0];
+    const double X = xin[p], Y = yin[p], r = P.r[p];
+    double nX = X, nY = Y;
+    double ux = P.ux[p], uy = P.uy[p], om = P.omega[p];
 
-    if (lane == 0) {
-        const double R = r + ph.cut_d;
-        const AxisTiles ax = axis_tiles(X, R, L.nx, TILE_W, L.ntx, L.per_x);
-        const AxisTiles ay = axis_tiles(Y, R, L.ny, TILE_H, L.nty, L.per_y);
+    if (integrate) {
+        // ---- 1. hydrodynamic force and torque
         double fx = 0.0, fy = 0.0, tq = 0.0;
-        for (int a = 0; a < ay.n; ++a)
-            for (int ty = ay.lo[a]; ty <= ay.hi[a]; ++ty)
-                for (int b = 0; b < ax.n; ++b)
-                    for (int tx = ax.lo[b]; tx <= ax.hi[b]; ++tx) {
-                        const int t = ty * L.ntx + tx;
-                        int n = B.count[t];
-                        n = n > MAXC ? MAXC : n;
-                        for (int s = 0; s < n; ++s)
-                            if (B.ids[t * MAXC + s] == p) {
-                                const double *q = B.partial + ((long long)t * MAXC + s) * 3;
-                                fx += q[0]; fy += q[1]; tq += q[2];
-                                break;
-                            }
-                    }
-        force[3 * p] = fx; force[3 * p + 1] = fy; force[3 * p + 2] = tq;
-    }
-
-    // particle-particle repulsion
-    double cx = 0.0, cy = 0.0;
-    const float xf = P.xf[p], yf = P.yf[p], rf = (float)r;
-    for (int j = lane; j < bp.np; j += 32) {
-        if (j == p) continue;
-        float dxf = xf - P.xf[j], dyf = yf - P.yf[j];
-        if (L.per_x) { if (dxf >= 0.5f * L.nx) dxf -= L.nx; else if (dxf < -0.5f * L.nx) dxf += L.nx; }
-        if (L.per_y) { if (dyf >= 0.5f * L.ny) dyf -= L.ny; else if (dyf < -0.5f * L.ny) dyf += L.ny; }
-        const float lim = rf + (float)P.r[j] + (float)bp.xi + 0.05f;
-        if (dxf * dxf + dyf * dyf > lim * lim) continue;
-        double dx = X - P.x[j], dy = Y - P.y[j];
-        if (L.per_x) { while (dx >= 0.5 * L.nx) dx -= L.nx; while (dx < -0.5 * L.nx) dx += L.nx; }
-        if (L.per_y) { while (dy >= 0.5 * L.ny) dy -= L.ny; while (dy < -0.5 * L.ny) dy += L.ny; }
-        const double d = sqrt(dx * dx + dy * dy), rr = r + P.r[j];
-        double s = 0.0;
-        if (d <= rr) s = (rr - d) / bp.eps_p2;
-        else if (d <= rr + bp.xi) s = (rr + bp.xi - d) * (rr + bp.xi - d) / bp.eps_p;
-        cx += s * dx;
-        cy += s * dy;
-    }
+        const int nk = bin_in.npslot[p];
+        for (int e = lane; e < nk * TILE_H; e += 32) {
+            const int k = e / TILE_H, row = e - k * TILE_H;
+            const int ts = bin_in.pslot[(long long)p * MAXT + k];
+            if (ts < 0) continue;
+            const int ty = (ts / MAXC) / L.ntx;
+            if (ty * TILE_H + row >= L.ny) continue;
+            const float4 v = partial[(long long)ts * TILE_H + row];
+            fx += (double)v.x; fy += (double)v.y; tq += (double)v.z;
+        }
+        // ---- 2. particle-particle repulsion.  A pair within r_i + r_j + xi
+        // shares the tile holding the middle of the gap between the surfaces
+        // (that point lies inside both binning reaches), so each lane takes
+        // some of this particle's tiles and counts a pair only in that tile;
+        // within a tile the pairs are added in increasing partner id.
+        double cx = 0.0, cy = 0.0;
+        const float xf = xfin[p], yf = yfin[p], rf = (float)r;
+        for (int k = lane; k < nk; k += 32) {
+            const int ts = bin_in.pslot[(long long)p * MAXT + k];
+            if (ts < 0) continue;
+            const int t = ts / MAXC;
+            int n = bin_in.count[t];
+            n = n > MAXC ? MAXC : n;
+            uint32_t contact = 0;
+            for (int sl = 0; sl < n; ++sl) {
+                const int j = bin_in.ids[t * MAXC + sl];
+                if (j == p) continue;
+                float dxf = xf - xfin[j], dyf = yf - yfin[j];
+                if (L.per_x) { if (dxf >= 0.5f * L.nx) dxf -= L.nx; else if (dxf < -0.5f * L.nx) dxf += L.nx; }
+                if (L.per_y) { if (dyf >= 0.5f * L.ny) dyf -= L.ny; else if (dyf < -0.5f * L.ny) dyf += L.ny; }
+                const float lim = rf + (float)P.r[j] + (float)bp.xi + 0.05f;
+                if (dxf * dxf + dyf * dyf > lim * lim) continue;
+                double dx = X - xin[j], dy = Y - yin[j];
+                if (L.per_x) { while (dx >= 0.5 * L.nx) dx -= L.nx; while (dx < -0.5 * L.nx) dx += L.nx; }
+                if (L.per_y) { while (dy >= 0.5 * L.ny) dy -= L.ny; while (dy < -0.5 * L.ny) dy += L.ny; }
+                // the middle of the gap between the two surfaces, at distance
+                // (d + r - r_j) / 2 from this centre toward the partner
+                const double dd = sqrt(dx * dx + dy * dy);
+                const double f = dd > 0.0 ? 0.5 * (dd + r - P.r[j]) / dd : 0.0;
+                double mx = X - f * dx, my = Y - f * dy;
+                if (L.per_x) { mx = fmod(mx, (double)L.nx); if (mx < 0.0) mx += L.nx; }
+                if (L.per_y) { my = fmod(my, (double)L.ny); if (my < 0.0) my += L.ny; }
+                int mxi = (int)floor(mx), myi = (int)floor(my);
+                mxi = mxi < 0 ? 0 : (mxi > L.nx - 1 ? L.nx - 1 : mxi);
+                myi = myi < 0 ? 0 : (myi > L.ny - 1 ? L.ny - 1 : myi);
+                if ((myi / TILE_H) * L.ntx + mxi / TILE_W == t) contact |= 1u << sl;
+            }
+            while (contact) {                         // increasing partner id
+                int sel = -1, jmin = 0x7fffffff;
+                for (uint32_t m = contact; m; m &= m - 1) {
+                    const int sl = __ffs(m) - 1, j = bin_in.ids[t * MAXC + sl];
+                    if (j < jmin) { jmin = j; sel = sl; }
+                }
+                contact &= ~(1u << sel);
+                double dx = X - xin[jmin], dy = Y - yin[jmin];
+                if (L.per_x) { while (dx >= 0.5 * L.nx) dx -= L.nx; while (dx < -0.5 * L.nx) dx += L.nx; }
+                if (L.per_y) { while (dy >= 0.5 * L.ny) dy -= L.ny; while (dy < -0.5 * L.ny) dy += L.ny; }
+                const double d = sqrt(dx * dx + dy * dy), rr = r + P.r[jmin];
+                double sc = 0.0;
+                if (d <= rr) sc = (rr - d) / bp.eps_p2;
+                else if (d <= rr + bp.xi) sc = (rr + bp.xi - d) * (rr + bp.xi - d) / bp.eps_p;
+                cx += sc * dx;
+                cy += sc * dy;
+            }
+        }
 #pragma unroll
-    for (int o = 16; o > 0; o >>= 1) {
-        cx += __shfl_xor_sync(0xffffffffu, cx, o);
-        cy += __shfl_xor_sync(0xffffffffu, cy, o);
-    }
-    if (lane == 0) {
+        for (int o = 16; o > 0; o >>= 1) {
+            fx += __shfl_xor_sync(0xffffffffu, fx, o);
+            fy += __shfl_xor_sync(0xffffffffu, fy, o);
+            tq += __shfl_xor_sync(0xffffffffu, tq, o);
+            cx += __shfl_xor_sync(0xffffffffu, cx, o);
+            cy += __shfl_xor_sync(0xffffffffu, cy, o);
+        }
         // wall repulsion: mirror image across each non-periodic wall
         for (int w = 0; w < 4; ++w) {
             if (L.side_kind[w] == SIDE_PERIODIC) continue;
@@ -531,56 +814,82 @@ __global__ void reduce_kernel(Lattice L, Physics ph, Particles P, Bins B, BodyPa
             if (w == NORTH) iy = 2.0 * (L.ny - 1) - Y;
             const double dx = X - ix, dy = Y - iy;
             const double d = sqrt(dx * dx + dy * dy), rr = 2.0 * r;
-            double s = 0.0;
-            if (d <= rr) s = (rr - d) / bp.eps_w2;
-            else if (d <= rr + bp.xi) s = (rr + bp.xi - d) * (rr + bp.xi - d) / bp.eps_w;
-            cx += s * dx;
-            cy += s * dy;
+            double sc = 0.0;
+            if (d <= rr) sc = (rr - d) / bp.eps_w2;
+            else if (d <= rr + bp.xi) sc = (rr + bp.xi - d) * (rr + bp.xi - d) / bp.eps_w;
+            cx += sc * dx;
+            cy += sc * dy;
         }
-        fcol[2 * p] = cx;
-        fcol[2 * p + 1] = cy;
+        // ---- 3. rigid-body update (every lane computes the same values)
+        if (!P.fixed[p]) {
+            const double m = P.rho_s[p] * 3.14159265358979323846 * r * r;
+            const double I = 0.5 * m * r * r;
+            const double wgt = (1.0 - bp.rho_f / P.rho_s[p]) * m;   // buoyancy-reduced weight / g
+            ux += (fx + cx + wgt * bp.gx) / m;
+            uy += (fy + cy + wgt * bp.gy) / m;
+            om += tq / I;
+            nX = X + ux;
+            nY = Y + uy;
+            if (L.per_x) { nX = fmod(nX, (double)L.nx); if (nX < 0.0) nX += L.nx; }
+            if (L.per_y) { nY = fmod(nY, (double)L.ny); if (nY < 0.0) nY += L.ny; }
+        }
+        if (lane == 0) {
+            force[3 * p] = fx; force[3 * p + 1] = fy; force[3 * p + 2] = tq;
+            fcol[2 * p] = cx; fcol[2 * p + 1] = cy;
+            if (!P.fixed[p]) {
+                P.ux[p] = ux; P.uy[p] = uy; P.omega[p] = om;
+                P.theta[p] += om;
+            }
+        }
     }
-}
+    if (lane == 0) {
+        xout[p] = nX; yout[p] = nY;
+        xfout[p] = (float)nX; yfout[p] = (float)nY;
+    }
 
-// One thread per particle: symplectic Euler of Eqs. 22-24 (dt = 1), then
-// binning of the particle into every tile its phi tail reaches.
-__global__ void integrate_bin_kernel(Lattice L, Physics ph, Particles P, Bins B, BodyParams bp,
-                                     const double *__restrict__ force, const double *__restrict__ fcol,
-                                     int integrate, int *__restrict__ err)
-{
-    const int p = blockIdx.x * blockDim.x + threadIdx.x;
-    if (p >= bp.np) return;
-    double X = P.x[p], Y = P.y[p];
-    const double r = P.r[p];
-    if (integrate && !P.fixed[p]) {
-        const double m = P.rho_s[p] * 3.14159265358979323846 * r * r;
-        const double I = 0.5 * m * r * r;
-        const double wgt = (1.0 - bp.rho_f / P.rho_s[p]) * m;   // buoyancy-reduced weight / g
-        double ux = P.ux[p] + (force[3 * p] + fcol[2 * p] + wgt * bp.gx) / m;
-        double uy = P.uy[p] + (force[3 * p + 1] + fcol[2 * p + 1] + wgt * bp.gy) / m;
-        double om = P.omega[p] + force[3 * p + 2] / I;
-        X += ux;
-        Y += uy;
-        if (L.per_x) { X = fmod(X, (double)L.nx); if (X < 0.0) X += L.nx; }
-        if (L.per_y) { Y = fmod(Y, (double)L.ny); if (Y < 0.0) Y += L.ny; }
-        P.ux[p] = ux; P.uy[p] = uy; P.omega[p] = om;
-        P.theta[p] += om;
-        P.x[p] = X; P.y[p] = Y;
-    }
-    P.xf[p] = (float)X;
-    P.yf[p] = (float)Y;
+    // ---- binning for the next sweep
+    // velocities as FP32 hi + lo: the sweep forms u_s - u*, a small difference
+    const float uxh = (float)ux, uyh = (float)uy, omh = (float)om;
+    const float4 rb = make_float4((float)r, uxh, uyh, omh);
+    const float4 rl = make_float4((float)(ux - (double)uxh), (float)(uy - (double)uyh), (float)(om - (double)omh), 0.f);
     const double R = r + ph.cut_d;
-    const AxisTiles ax = axis_tiles(X, R, L.nx, TILE_W, L.ntx, L.per_x);
-    const AxisTiles ay = axis_tiles(Y, R, L.ny, TILE_H, L.nty, L.per_y);
-    for (int a = 0; a < ay.n; ++a)
-        for (int ty = ay.lo[a]; ty <= ay.hi[a]; ++ty)
-            for (int b = 0; b < ax.n; ++b)
-                for (int tx = ax.lo[b]; tx <= ax.hi[b]; ++tx) {
-                    const int t = ty * L.ntx + tx;
-                    const int s = atomicAdd(&B.count[t], 1);
-                    if (s < MAXC) B.ids[t * MAXC + s] = p;
-                    else atomicOr(err, ERR_OVERFLOW);
-                }
+    const AxisTiles ax = axis_tiles(nX, R, L.nx, TILE_W, L.ntx, L.per_x);
+    const AxisTiles ay = axis_tiles(nY, R, L.ny, TILE_H, L.nty, L.per_y);
+    const int NX = range_len(ax), NY = range_len(ay);
+    int total = NX * NY;
+    if (total > MAXT) {                      // ruled out at create; kept as a guard
+        if (lane == 0) atomicOr(err, ERR_OVERFLOW);
+        total = MAXT;
+    }
+    for (int k = lane; k < total; k += 32) {
+        const int ty = range_at(ay, k / NX), tx = range_at(ax, k - (k / NX) * NX);
+        const int t = ty * L.ntx + tx;
+        const int s = atomicAdd(&bin_out.count[t], 1);
+        int entry = -1;
+        if (s < MAXC) {
+            double cx = nX - (double)(tx * TILE_W), cy = nY - (double)(ty * TILE_H);
+            if (L.per_x) {
+                const double h = 0.5 * TILE_W;
+                while (cx - h >= 0.5 * L.nx) cx -= L.nx;
+                while (cx - h < -0.5 * L.nx) cx += L.nx;
+            }
+            if (L.per_y) {
+                const double h = 0.5 * TILE_H;
+                while (cy - h >= 0.5 * L.ny) cy -= L.ny;
+                while (cy - h < -0.5 * L.ny) cy += L.ny;
+            }
+            const float cxh = (float)cx, cyh = (float)cy;
+            entry = t * MAXC + s;
+            bin_out.ids[entry] = p;
+            bin_out.rec[NREC * (long long)entry] = make_float4(cxh, (float)(cx - (double)cxh), cyh, (float)(cy - (double)cyh));
+            bin_out.rec[NREC * (long long)entry + 1] = rb;
+            bin_out.rec[NREC * (long long)entry + 2] = rl;
+        } else {
+            atomicOr(err, ERR_OVERFLOW);
+        }
+        bin_out.pslot[(long long)p * MAXT + k] = entry;
+    }
+    if (lane == 0) bin_out.npslot[p] = total;
 }
 
 // ------------------------------------------------------------ conversions
@@ -614,18 +923,16 @@ __global__ void import_kernel(T *__restrict__ dst, Lattice L, const double *__re
 template <typename T>
 __global__ void init_kernel(T *__restrict__ dst, Lattice L, float drho, float ux, float uy) {
     const long long n = (long long)L.nx * L.ny;
-    const float rho = 1.0f + drho, usq = ux * ux + uy * uy;
+    float e[9];
+    eq_dev9(drho, 1.0f + drho, ux, uy, e);
     for (long long k = blockIdx.x * (long long)blockDim.x + threadIdx.x; k < 9 * n; k += (long long)gridDim.x * blockDim.x) {
         const int i = (int)(k / n);
         const long long r = k - i * n;
         const int y = (int)(r / L.nx), x = (int)(r - (long long)y * L.nx);
-        float v = 0.f;
-        switch (i) {
-#define DILBM_CASE(I) case I: v = eq_dev(I, drho, rho, ux, uy, usq); break;
-            DILBM_CASE(0) DILBM_CASE(1) DILBM_CASE(2) DILBM_CASE(3) DILBM_CASE(4)
-            DILBM_CASE(5) DILBM_CASE(6) DILBM_CASE(7) DILBM_CASE(8)
-#undef DILBM_CASE
-        }
+        float v = e[0];
+#pragma unroll
+        for (int j = 1; j < 9; ++j)
+            if (i == j) v = e[j];
         Storage<T>::store1(dst + i * L.plane + (long long)y * L.pitch + x, v);
     }
 }
