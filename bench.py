@@ -214,6 +214,23 @@ def measured_peak_hbm():
         return 6800.0, "fallback"
 
 
+def measured_traffic(key):
+    """DRAM bytes per sweep launch from a committed ncu summary, if it was
+    taken on the current kernel source (else None)."""
+    import glob
+    import hashlib
+    import re
+    src = os.path.join(ROOT, "paper_2106_08950_gb300", "csrc", "dilbm_kernels.cuh")
+    with open(src, "rb") as fh:
+        sha = hashlib.sha256(fh.read()).hexdigest()[:16]
+    for path in glob.glob(os.path.join(ROOT, "profiles", "*.md")):
+        with open(path) as fh:
+            for m in re.finditer(r"<!-- traffic (\S+) (\d+) sha256=(\w+) -->", fh.read()):
+                if m.group(1) == key and m.group(3) == sha:
+                    return int(m.group(2))
+    return None
+
+
 def gpu_arm(args):
     import ctypes as C
 
@@ -290,15 +307,7 @@ def gpu_arm(args):
     per_launch_ms = sweep_ms / max(sweep_n, 1)
     alg_bytes = BYTES_PER_NODE[args.storage] * nodes
     achieved = alg_bytes / (per_launch_ms / 1e3) / 1e9
-    traffic = None
-    tpath = os.path.join(ROOT, "profiles", "sweep_traffic.json")
-    try:
-        with open(tpath) as fh:
-            tr = json.load(fh)
-        key = f"{args.workload}:{args.storage}:{prob.nx}x{prob.ny}"
-        traffic = tr.get(key)
-    except (OSError, ValueError):
-        traffic = None
+    traffic = measured_traffic(f"{args.workload}:{args.storage}:{prob.nx}x{prob.ny}")
     roof = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
             "traffic": traffic, "peak_kind": peak_kind,
             "kernel": "sweep_kernel", "sweep_ms_per_launch": per_launch_ms,

@@ -712,7 +712,7 @@ __device__ __forceinline__ int range_len(const AxisTiles &a) {
 // reaches (lanes take the tiles in a fixed order), with the record the sweep
 // reads: the centre relative to the tile origin (minimum image about the tile
 // centre) as FP32 hi + lo, radius and velocities.
-__global__ void particles_kernel(Lattice L, Physics ph, Particles P, BodyParams bp, Bins bin_in, Bins bin_out,
+static __global__ void particles_kernel(Lattice L, Physics ph, Particles P, BodyParams bp, Bins bin_in, Bins bin_out,
                                  const float4 *__restrict__ partial, int pin, int pout, int integrate,
                                  double *__restrict__ force, double *__restrict__ fcol, int *__restrict__ err)
 {
