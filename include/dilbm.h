@@ -168,6 +168,52 @@ int dilbm_set_timing(dilbm_ctx *ctx, int enable);
 int dilbm_sweep_time(dilbm_ctx *ctx, double *ms_total, long long *launches);
 long long dilbm_launch_count(const dilbm_ctx *ctx);
 
+/*
+ * One time step that allocates no device memory.  The paper has no
+ * counterpart: this is a calling convention, not part of the method.
+ *
+ * For callers that cannot call cudaMalloc where they need a step: a solver
+ * that owns a fixed device memory pool and allows no further allocations, a
+ * stream-ordered pipeline in which an allocation would synchronise the device,
+ * or a host that has budgeted every byte of the GPU in advance.  It runs the
+ * same kernels as dilbm_step; their scratch memory (tile bins, force
+ * partials, particle state in structure-of-arrays form, the error word) lives
+ * in one static device array of about 8 MB compiled into the library, which
+ * every GPU that loads the library holds until the process exits.
+ *
+ *   grid, tau, interface_width  as for dilbm_create; storage must be DILBM_FP32.
+ *   f_in   device, DILBM_STATIC_POP_FLOATS(nx, ny) floats: the post-collision
+ *          populations as deviations f_i - w_i (w_i the FP32 weights of Eq. 4),
+ *          plane i of ny rows of DILBM_STATIC_PITCH(nx) floats, starting
+ *          DILBM_STATIC_POP_OFFSET floats into the buffer; the
+ *          DILBM_STATIC_POP_OFFSET floats before and after the planes must be
+ *          readable (their values are never used).  Not modified.
+ *   f_out  device, same size and layout, receives the next step's
+ *          populations; must not alias f_in.
+ *   particles, np  device array of np dilbm_particle, read and updated in
+ *          place (np <= DILBM_STATIC_MAX_PARTICLES).
+ *   force  device, np x 3 doubles: force and torque of this step (Eqs. 18-19).
+ *   cuda_stream  stream for all work.
+ * Limits: ceil(nx/128) * ceil(ny/8) <= DILBM_STATIC_MAX_TILES tiles and
+ * np <= DILBM_STATIC_MAX_PARTICLES; larger problems are rejected with
+ * DILBM_ERR_INVALID_ARG before any work is queued (use dilbm_create for them).
+ * Every call shares the static array: the call clears what must start at zero
+ * (bin counts, error word) but calls that overlap on the GPU (other streams,
+ * other host threads) race on it and must not be issued.  The first call on a
+ * device looks up the array's device address with that device current; make
+ * that first call before any stream capture.  The call ends by synchronising
+ * the stream to read the error word; it returns DILBM_OK or
+ * INVALID_ARG / CUDA / UNSTABLE / TIMEOUT / OVERFLOW, with the message in
+ * dilbm_last_error().
+ */
+#define DILBM_STATIC_MAX_TILES 1024
+#define DILBM_STATIC_MAX_PARTICLES 256
+#define DILBM_STATIC_PITCH(nx) ((((nx) + 31) / 32) * 32)
+#define DILBM_STATIC_POP_OFFSET 256
+#define DILBM_STATIC_POP_FLOATS(nx, ny) (9LL * (ny) * DILBM_STATIC_PITCH(nx) + 2 * DILBM_STATIC_POP_OFFSET)
+int dilbm_step_static(const dilbm_grid *grid, double tau, double interface_width, const float *f_in,
+                      float *f_out, dilbm_particle *particles, int np, double *force, void *cuda_stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -239,6 +239,11 @@ int read_sticky(dilbm_ctx *c) {
 
 }  // namespace
 
+namespace dilbm {
+// Lets other translation units of the library report through dilbm_last_error().
+int set_last_error(int code, const std::string &msg) { return fail(code, msg); }
+}  // namespace dilbm
+
 extern "C" {
 
 const char *dilbm_last_error(void) { return g_err.c_str(); }
