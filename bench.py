@@ -43,7 +43,7 @@ def parse():
     ap.add_argument("--steps", type=int, default=4000)
     ap.add_argument("--warmup", type=int, default=20)
     ap.add_argument("--impl", default="dilbm", choices=["dilbm", "reference"])
-    ap.add_argument("--workload", default="periodic", choices=["periodic", "sedimentation", "cylinder"])
+    ap.add_argument("--workload", default="periodic", choices=["periodic", "sedimentation", "cylinder", "batch"])
     ap.add_argument("--storage", default="fp32", choices=["fp32", "fp16", "bf16"])
     ap.add_argument("--size", type=int, default=4096, help="periodic box edge")
     ap.add_argument("--particles", type=int, default=2048)
@@ -337,10 +337,102 @@ def gpu_arm(args):
     return 0
 
 
+def batch_arm(args):
+    """64 uneven lattices (seed 4) advanced together by the batched launch,
+    against the same lattices stepped one at a time."""
+    import torch
+    from paper_2106_08950_gb300 import dilbm as D
+    from paper_2106_08950_gb300 import workloads as W
+
+    world, rank, local = dist_env()
+    torch.cuda.set_device(local)
+    dist = init_dist(world, "nccl")
+    dev = torch.device("cuda", local)
+    jobs = W.batch_lattices(seed=4 + 1000 * rank)
+    nodes = sum(j.nodes for j in jobs)
+    stream = torch.cuda.Stream(device=dev)
+    sh = int(stream.cuda_stream)
+    members = [D.Simulation(j, storage=args.storage, stream=sh) for j in jobs]
+    batch = D.Batch(members)
+    batch.step(args.warmup)
+    batch.sync()
+
+    clocks = ClockSampler(local)
+    clocks.start()
+    time.sleep(0.3)
+    barrier(dist)
+    torch.cuda.synchronize()
+    l0 = batch.launches
+    t0 = time.perf_counter()
+    batch.step(args.steps)
+    batch.sync()
+    dt = time.perf_counter() - t0
+    launches = batch.launches - l0
+    clk = clocks.stop()
+    dt = max_over_ranks(dist, dt, dev)
+    value = nodes * args.steps * world / dt / 1e6
+
+    # the batched sweep alone, timed by CUDA events (direct launches)
+    k_t = max(10, min(args.steps, 200))
+    batch.set_timing(True)
+    batch.step(k_t)
+    sweep_ms, sweep_n = batch.sweep_time()
+    batch.set_timing(False)
+    batch.sync()
+
+    # the same lattices one at a time, each for the same number of steps
+    k_alone = max(10, min(args.steps, 200))
+    alone = [D.Simulation(j, storage=args.storage, stream=sh) for j in jobs]
+    for a in alone:
+        a.step(args.warmup)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for a in alone:
+        a.step(k_alone)
+    for a in alone:
+        a.sync()
+    dt_alone = time.perf_counter() - t0
+    alone_value = nodes * k_alone / dt_alone / 1e6
+
+    peak, peak_kind = measured_peak_hbm()
+    per_launch = sweep_ms / max(sweep_n, 1)
+    alg = BYTES_PER_NODE[args.storage] * nodes
+    achieved = alg / (per_launch / 1e3) / 1e9
+    line = {"metric": METRIC, "value": value, "unit": "MLUPS", "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": dt / args.steps * 1e3, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None,
+            "dtype": {"fp32": "f32", "fp16": "f16-storage/f32-math", "bf16": "bf16-storage/f32-math"}[args.storage],
+            "data": "synthetic",
+            "config": {"workload": "batch of 64 uneven lattices (seed 4): nx log-U[128,1024], ny log-U[128,2048], "
+                                   "cylinder or sedimentation jobs, 1-32 discs r U[5,15], Re log-U[10,100]",
+                       "storage": args.storage, "nodes": nodes, "lattices": len(jobs),
+                       "particles": sum(len(j.particles) for j in jobs),
+                       "launch": "one batched sweep + one batched particle launch per step, CUDA-graph replay",
+                       "l2": f"{nodes * BYTES_PER_NODE[args.storage] / 1e6:.0f} MB of populations per step"},
+            "one_at_a_time": {"value": alone_value, "unit": "MLUPS", "steps": k_alone,
+                              "speedup_of_batch": value / alone_value},
+            "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+                         "traffic": None, "peak_kind": peak_kind, "kernel": "sweep_kernel (batched)",
+                         "sweep_ms_per_launch": per_launch, "algorithmic_bytes_per_launch": alg},
+            "gpu_launches": launches, "e2e": None, "clocks": clk}
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    for a in alone:
+        a.close()
+    batch.close()
+    for m in members:
+        m.close()
+    if dist is not None:
+        dist.destroy_process_group()
+    return 0
+
+
 def main():
     args = parse()
     if args.impl == "reference":
         return reference_arm(args)
+    if args.workload == "batch":
+        return batch_arm(args)
     return gpu_arm(args)
 
 

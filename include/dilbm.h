@@ -169,6 +169,34 @@ int dilbm_sweep_time(dilbm_ctx *ctx, double *ms_total, long long *launches);
 long long dilbm_launch_count(const dilbm_ctx *ctx);
 
 /*
+ * Batches: many contexts advanced together (the same equations, Eqs. 13-19,
+ * 22-24, 28-29, on every member).  One step of a batch is one sweep launch
+ * over the concatenated row segments of all members and one particle launch
+ * over all their particles, replayed from CUDA graphs captured at create;
+ * every member's result is bit for bit the one dilbm_step gives it alone.
+ *
+ * dilbm_batch_create: members[0..n-1] (1 <= n <= 1024 distinct contexts, all
+ *   with the same storage; they stay owned by the caller and must outlive the
+ *   batch).  The batch runs on a private stream ordered after, and before,
+ *   each member's own stream by events, so member calls (forces, fields,
+ *   dilbm_step) may be mixed with batch steps.  cuda_stream is unused.
+ * dilbm_batch_step: advance every member nsteps (asynchronous).
+ * dilbm_batch_sync: wait; return the first member's sticky device error and
+ *   its index in *first_failed (-1 if none; pointer may be NULL).
+ * dilbm_batch_set_timing / dilbm_batch_sweep_time: CUDA events around every
+ *   batched sweep launch (timing replaces graph replay by direct launches).
+ * dilbm_batch_launch_count: kernels the batch has launched.
+ */
+typedef struct dilbm_batch dilbm_batch;
+int dilbm_batch_create(dilbm_ctx *const *members, int n, void *cuda_stream, dilbm_batch **out);
+int dilbm_batch_step(dilbm_batch *batch, long long nsteps);
+int dilbm_batch_sync(dilbm_batch *batch, int *first_failed);
+int dilbm_batch_set_timing(dilbm_batch *batch, int enable);
+int dilbm_batch_sweep_time(dilbm_batch *batch, double *ms_total, long long *launches);
+long long dilbm_batch_launch_count(const dilbm_batch *batch);
+void dilbm_batch_destroy(dilbm_batch *batch);
+
+/*
  * One time step that allocates no device memory.  The paper has no
  * counterpart: this is a calling convention, not part of the method.
  *

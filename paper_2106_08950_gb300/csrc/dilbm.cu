@@ -5,6 +5,7 @@
 
 #include <cmath>
 #include <cstdio>
+#include <cstdlib>
 #include <cstring>
 #include <string>
 #include <vector>
@@ -119,11 +120,29 @@ int check_reach(dilbm_ctx *c, const dilbm_particle *p, int np) {
     return DILBM_OK;
 }
 
+PartArgs particle_args(const dilbm_ctx *c, int cur, int integrate) {
+    const int nxt = integrate ? cur ^ 1 : cur;
+    PartArgs a{};
+    a.L = c->L;
+    a.ph = c->ph;
+    a.P = c->P;
+    a.bp = c->bp;
+    a.bin_in = c->bins[cur];
+    a.bin_out = c->bins[nxt];
+    a.partial = c->partial;
+    a.pin = cur;
+    a.pout = nxt;
+    a.integrate = integrate;
+    a.force = c->force;
+    a.fcol = c->fcol;
+    a.err = c->err;
+    return a;
+}
+
 int launch_particles(dilbm_ctx *c, int integrate) {
-    const int np = c->np, cur = c->cur, nxt = integrate ? cur ^ 1 : cur;
-    particles_kernel<<<(np * 32 + 127) / 128, 128, 0, c->stream>>>(
-        c->L, c->ph, c->P, c->bp, c->bins[cur], c->bins[nxt], c->partial, cur, nxt, integrate, c->force, c->fcol,
-        c->err);
+    const int np = c->np;
+    particles_kernel<false><<<(np * 32 + 127) / 128, 128, 0, c->stream>>>(particle_args(c, c->cur, integrate),
+                                                                          nullptr, BatchIndex{});
     DILBM_CUDA(cudaGetLastError());
     c->launches += 1;
     return DILBM_OK;
@@ -154,32 +173,57 @@ int upload_particles(dilbm_ctx *c, const dilbm_particle *p, int np) {
     return DILBM_OK;
 }
 
-// Persistent grid: as many blocks as fit on the device at once (queried per
-// kernel instantiation), but no more than the row segments need.
-template <typename T, int MODE, bool EDGES>
-cudaError_t launch_sweep_k(dilbm_ctx *c, const void *src, void *dst, FieldsOut fo) {
-    static int per_sm[64] = {};     // blocks per SM, per device ordinal
+template <typename T>
+SweepArgs<T> sweep_args(const dilbm_ctx *c, int cur, const void *src, void *dst, bool clear, FieldsOut fo) {
+    SweepArgs<T> a{};
+    a.src = (const T *)src;
+    a.dst = (T *)dst;
+    a.L = c->L;
+    a.ph = c->ph;
+    a.B = c->bins[cur];
+    a.partial = c->partial;
+    a.clear = (clear && c->np > 0) ? c->bins[cur ^ 1].count : nullptr;
+    a.err = c->err;
+    a.fo = fo;
+    return a;
+}
+
+// Blocks of a sweep kernel resident per SM (queried once per device and
+// kernel) after opting in to its dynamic shared memory.
+template <typename K>
+cudaError_t sweep_occupancy(K kern, int *per_sm_cache, int *per_sm_out) {
     int dev = 0;
     cudaError_t e = cudaGetDevice(&dev);
     if (e != cudaSuccess) return e;
-    const size_t smem = sweep_smem_bytes<T>();
-    auto kern = sweep_kernel<T, MODE, EDGES>;
-    if (dev < 64 && per_sm[dev] == 0) {
+    if (dev >= 64) return cudaErrorInvalidDevice;
+    if (per_sm_cache[dev] == 0) {
+        const size_t smem = sweep_smem_bytes<float>() > sweep_smem_bytes<__half>() ? sweep_smem_bytes<float>()
+                                                                                    : sweep_smem_bytes<__half>();
         e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e != cudaSuccess) return e;
         int n = 0;
         e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, kern, SWEEP_WARPS * 32, smem);
         if (e != cudaSuccess) return e;
-        per_sm[dev] = n > 0 ? n : 1;
+        per_sm_cache[dev] = n > 0 ? n : 1;
     }
+    *per_sm_out = per_sm_cache[dev];
+    return cudaSuccess;
+}
+
+// Persistent grid: as many blocks as fit on the device at once, but no more
+// than the row segments need.
+template <typename T, int MODE, bool EDGES>
+cudaError_t launch_sweep_k(dilbm_ctx *c, const void *src, void *dst, FieldsOut fo) {
+    static int cache[64] = {};
+    int per_sm = 1;
+    cudaError_t e = sweep_occupancy(sweep_kernel<T, MODE, EDGES>, cache, &per_sm);
+    if (e != cudaSuccess) return e;
     const long long items = (long long)c->L.ny * c->L.ntx;
-    long long blocks = (long long)c->num_sms * (dev < 64 ? per_sm[dev] : 1);
+    long long blocks = (long long)c->num_sms * per_sm;
     const long long need = (items + SWEEP_WARPS - 1) / SWEEP_WARPS;
     if (blocks > need) blocks = need;
-    const int cur = c->cur;
-    kern<<<(unsigned)blocks, SWEEP_WARPS * 32, smem, c->stream>>>(
-        (const T *)src, (T *)dst, c->L, c->ph, c->bins[cur], c->partial,
-        (MODE == MODE_STEP && c->np > 0) ? c->bins[cur ^ 1].count : nullptr, fo, c->err);
+    sweep_kernel<T, MODE, EDGES><<<(unsigned)blocks, SWEEP_WARPS * 32, sweep_smem_bytes<T>(), c->stream>>>(
+        sweep_args<T>(c, c->cur, src, dst, MODE == MODE_STEP, fo));
     return cudaGetLastError();
 }
 
@@ -524,5 +568,328 @@ int dilbm_sweep_time(dilbm_ctx *c, double *ms_total, long long *launches) {
 }
 
 long long dilbm_launch_count(const dilbm_ctx *c) { return c ? c->launches : -1; }
+
+}  // extern "C"
+
+// ---------------------------------------------------------------- batches
+// Many lattices advanced together: one sweep launch over the concatenated row
+// segments of every member and one particle launch over all their particles
+// per step, replayed from CUDA graphs.
+struct dilbm_batch {
+    std::vector<dilbm_ctx *> members;
+    std::vector<int> cur0;              // members' parity when the launches were captured
+    int storage = DILBM_FP32;
+    long long done = 0;                 // batch steps since the capture
+    cudaStream_t stream = nullptr;      // private stream the graphs run on
+    cudaEvent_t ev_in = nullptr, ev_out = nullptr;
+    std::vector<cudaStream_t> member_streams;
+    std::vector<void *> sweep_params[2];   // BatchArgs<T> per launch group, per phase (host copies)
+    PartArgs *part_args[2] = {nullptr, nullptr};
+    int *part_start = nullptr;          // n + 1
+    int nparts = 0;
+    std::vector<int> group_blocks;      // persistent grid of each launch group
+    cudaGraphExec_t g_pair = nullptr, g_single[2] = {nullptr, nullptr};
+    bool timing = false;
+    std::vector<cudaEvent_t> ev;
+    size_t ev_used = 0;
+    long long launches = 0;
+};
+
+namespace {
+
+constexpr int MAX_BATCH = 1024;
+
+void free_sweep_params(dilbm_batch *b) {
+    for (int phase = 0; phase < 2; ++phase) {
+        for (void *q : b->sweep_params[phase]) std::free(q);
+        b->sweep_params[phase].clear();
+    }
+}
+
+// Host copies of the batched sweep's parameters: members in groups of at
+// most BATCH_LAUNCH_MAX, both phases (the second step of a pair runs every
+// member at the other parity).
+template <typename T>
+void build_sweep_params(dilbm_batch *b) {
+    free_sweep_params(b);
+    const int n = (int)b->members.size();
+    b->group_blocks.clear();
+    for (int g0 = 0; g0 < n; g0 += BATCH_LAUNCH_MAX) {
+        const int gn = n - g0 < BATCH_LAUNCH_MAX ? n - g0 : BATCH_LAUNCH_MAX;
+        int items = 0;
+        for (int phase = 0; phase < 2; ++phase) {
+            BatchArgs<T> *ba = static_cast<BatchArgs<T> *>(std::calloc(1, sizeof(BatchArgs<T>)));
+            ba->n = gn;
+            ba->item_start[0] = ba->tile_start[0] = 0;
+            for (int k = 0; k < gn; ++k) {
+                const dilbm_ctx *c = b->members[g0 + k];
+                const int cur = b->cur0[g0 + k] ^ phase;
+                ba->a[k] = sweep_args<T>(c, cur, c->buf[cur], c->buf[cur ^ 1], true, FieldsOut{});
+                ba->item_start[k + 1] = ba->item_start[k] + c->L.ny * c->L.ntx;
+                ba->tile_start[k + 1] = ba->tile_start[k] + c->L.ntx * c->L.nty;
+            }
+            items = ba->item_start[gn];
+            b->sweep_params[phase].push_back(ba);
+        }
+        b->group_blocks.push_back(items);    // converted to a grid size by the caller
+    }
+}
+
+int upload_part_args(dilbm_batch *b) {
+    const size_t n = b->members.size();
+    for (int phase = 0; phase < 2; ++phase) {
+        std::vector<PartArgs> pa(n);
+        for (size_t k = 0; k < n; ++k) pa[k] = particle_args(b->members[k], b->cur0[k] ^ phase, 1);
+        DILBM_CUDA(cudaMemcpyAsync(b->part_args[phase], pa.data(), sizeof(PartArgs) * n, cudaMemcpyHostToDevice, b->stream));
+        DILBM_CUDA(cudaStreamSynchronize(b->stream));
+    }
+    return DILBM_OK;
+}
+
+template <typename T>
+cudaError_t launch_batch_sweep(dilbm_batch *b, int phase) {
+    for (size_t g = 0; g < b->sweep_params[phase].size(); ++g) {
+        const BatchArgs<T> &ba = *static_cast<const BatchArgs<T> *>(b->sweep_params[phase][g]);
+        sweep_batch_kernel<T, MODE_STEP><<<b->group_blocks[g], SWEEP_WARPS * 32, sweep_smem_bytes<T>(), b->stream>>>(ba);
+        cudaError_t e = cudaGetLastError();
+        if (e != cudaSuccess) return e;
+    }
+    return cudaSuccess;
+}
+
+// One batch step at `phase`: the sweep over every member, then the particles.
+int batch_phase(dilbm_batch *b, int phase) {
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    if (b->timing) {
+        if (b->ev_used + 2 > b->ev.size())
+            for (int k = 0; k < 64; ++k) {
+                cudaEvent_t e;
+                DILBM_CUDA(cudaEventCreate(&e));
+                b->ev.push_back(e);
+            }
+        e0 = b->ev[b->ev_used];
+        e1 = b->ev[b->ev_used + 1];
+        b->ev_used += 2;
+        DILBM_CUDA(cudaEventRecord(e0, b->stream));
+    }
+    cudaError_t e;
+    if (b->storage == DILBM_FP32) e = launch_batch_sweep<float>(b, phase);
+    else if (b->storage == DILBM_FP16_DEV) e = launch_batch_sweep<__half>(b, phase);
+    else e = launch_batch_sweep<__nv_bfloat16>(b, phase);
+    if (e != cudaSuccess) return cuda_fail(e, "batched sweep_kernel launch");
+    if (b->timing) DILBM_CUDA(cudaEventRecord(e1, b->stream));
+    b->launches += (long long)b->sweep_params[phase].size();
+    if (b->nparts > 0) {
+        BatchIndex pi{b->part_start, nullptr, (int)b->members.size()};
+        particles_kernel<true><<<(b->nparts * 32 + 127) / 128, 128, 0, b->stream>>>(PartArgs{}, b->part_args[phase], pi);
+        DILBM_CUDA(cudaGetLastError());
+        b->launches += 1;
+    }
+    return DILBM_OK;
+}
+
+int capture(dilbm_batch *b, int first_phase, int nphases, cudaGraphExec_t *out) {
+    if (*out) {
+        cudaGraphExecDestroy(*out);
+        *out = nullptr;
+    }
+    cudaGraph_t g = nullptr;
+    const long long l0 = b->launches;
+    DILBM_CUDA(cudaStreamBeginCapture(b->stream, cudaStreamCaptureModeThreadLocal));
+    int rc = DILBM_OK;
+    for (int k = 0; k < nphases && rc == DILBM_OK; ++k) rc = batch_phase(b, (first_phase + k) & 1);
+    cudaError_t e = cudaStreamEndCapture(b->stream, &g);
+    b->launches = l0;    // capturing launches nothing
+    if (rc) {
+        if (g) cudaGraphDestroy(g);
+        return rc;
+    }
+    if (e != cudaSuccess) return cuda_fail(e, "cudaStreamEndCapture");
+    e = cudaGraphInstantiate(out, g, 0);
+    cudaGraphDestroy(g);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaGraphInstantiate");
+    return DILBM_OK;
+}
+
+// (Re)build every launch of the batch from the members' current parity:
+// sweep parameters, particle descriptors and the three graphs.
+int prepare_batch(dilbm_batch *b) {
+    for (size_t k = 0; k < b->members.size(); ++k) b->cur0[k] = b->members[k]->cur;
+    b->done = 0;
+    if (b->storage == DILBM_FP32) build_sweep_params<float>(b);
+    else if (b->storage == DILBM_FP16_DEV) build_sweep_params<__half>(b);
+    else build_sweep_params<__nv_bfloat16>(b);
+    static int cache32[64] = {}, cache16[64] = {}, cacheb[64] = {};
+    int per_sm = 1;
+    cudaError_t e;
+    if (b->storage == DILBM_FP32) e = sweep_occupancy(sweep_batch_kernel<float, MODE_STEP>, cache32, &per_sm);
+    else if (b->storage == DILBM_FP16_DEV) e = sweep_occupancy(sweep_batch_kernel<__half, MODE_STEP>, cache16, &per_sm);
+    else e = sweep_occupancy(sweep_batch_kernel<__nv_bfloat16, MODE_STEP>, cacheb, &per_sm);
+    if (e != cudaSuccess) return cuda_fail(e, "batched sweep occupancy");
+    for (int &items : b->group_blocks) {
+        const long long full = (long long)b->members[0]->num_sms * per_sm;
+        const long long need = (items + SWEEP_WARPS - 1) / SWEEP_WARPS;
+        items = (int)(need < full ? (need > 0 ? need : 1) : full);
+    }
+    int rc;
+    if ((rc = upload_part_args(b))) return rc;
+    if ((rc = capture(b, 0, 2, &b->g_pair)) || (rc = capture(b, 0, 1, &b->g_single[0])) ||
+        (rc = capture(b, 1, 1, &b->g_single[1])))
+        return rc;
+    return DILBM_OK;
+}
+
+// Kernels launched by one batch step (sweep groups + particles).
+int batch_launches_per_step(const dilbm_batch *b) {
+    return (int)b->sweep_params[0].size() + (b->nparts > 0 ? 1 : 0);
+}
+
+}  // namespace
+
+extern "C" {
+
+int dilbm_batch_create(dilbm_ctx *const *members, int n, void *cuda_stream, dilbm_batch **out) {
+    (void)cuda_stream;
+    if (!members || !out || n < 1 || n > MAX_BATCH)
+        return fail(DILBM_ERR_INVALID_ARG, "a batch takes 1.." + std::to_string(MAX_BATCH) + " contexts");
+    *out = nullptr;
+    for (int k = 0; k < n; ++k) {
+        if (!members[k]) return fail(DILBM_ERR_INVALID_ARG, "NULL member context");
+        if (members[k]->storage != members[0]->storage)
+            return fail(DILBM_ERR_INVALID_ARG, "all members of a batch must use the same storage");
+        for (int j = 0; j < k; ++j)
+            if (members[j] == members[k]) return fail(DILBM_ERR_INVALID_ARG, "a context appears twice in the batch");
+    }
+    dilbm_batch *b = new dilbm_batch();
+    auto bail = [&](int code) { dilbm_batch_destroy(b); return code; };
+    b->members.assign(members, members + n);
+    b->cur0.resize(n);
+    b->storage = members[0]->storage;
+    cudaError_t e;
+    if ((e = cudaStreamCreateWithFlags(&b->stream, cudaStreamNonBlocking)) != cudaSuccess ||
+        (e = cudaEventCreateWithFlags(&b->ev_in, cudaEventDisableTiming)) != cudaSuccess ||
+        (e = cudaEventCreateWithFlags(&b->ev_out, cudaEventDisableTiming)) != cudaSuccess)
+        return bail(cuda_fail(e, "batch stream/events"));
+    for (int k = 0; k < n; ++k) {
+        bool seen = false;
+        for (cudaStream_t s : b->member_streams) seen |= s == members[k]->stream;
+        if (!seen) b->member_streams.push_back(members[k]->stream);
+    }
+    // particles of each member, in one list
+    std::vector<int> ps(n + 1, 0);
+    for (int k = 0; k < n; ++k) ps[k + 1] = ps[k] + members[k]->np;
+    b->nparts = ps[n];
+    for (int phase = 0; phase < 2; ++phase)
+        if ((e = cudaMalloc((void **)&b->part_args[phase], sizeof(PartArgs) * n)) != cudaSuccess)
+            return bail(cuda_fail(e, "cudaMalloc batch descriptors"));
+    if ((e = cudaMalloc((void **)&b->part_start, sizeof(int) * (n + 1))) != cudaSuccess ||
+        (e = cudaMemcpy(b->part_start, ps.data(), sizeof(int) * (n + 1), cudaMemcpyHostToDevice)) != cudaSuccess)
+        return bail(cuda_fail(e, "batch particle list"));
+    // order after every member's queued work, then build the launches
+    for (cudaStream_t s : b->member_streams) {
+        if ((e = cudaEventRecord(b->ev_in, s)) != cudaSuccess || (e = cudaStreamWaitEvent(b->stream, b->ev_in, 0)) != cudaSuccess)
+            return bail(cuda_fail(e, "batch stream ordering"));
+    }
+    int rc;
+    if ((rc = prepare_batch(b))) return bail(rc);
+    *out = b;
+    return DILBM_OK;
+}
+
+int dilbm_batch_step(dilbm_batch *b, long long nsteps) {
+    if (!b || nsteps < 0) return fail(DILBM_ERR_INVALID_ARG, "bad batch or step count");
+    if (nsteps == 0) return DILBM_OK;
+    cudaError_t e;
+    // a member stepped on its own since the descriptors were built: rebuild
+    bool stale = false;
+    for (size_t k = 0; k < b->members.size(); ++k)
+        stale |= b->members[k]->cur != (b->cur0[k] ^ (int)(b->done & 1));
+    for (cudaStream_t s : b->member_streams) {
+        if ((e = cudaEventRecord(b->ev_in, s)) != cudaSuccess || (e = cudaStreamWaitEvent(b->stream, b->ev_in, 0)) != cudaSuccess)
+            return cuda_fail(e, "batch stream ordering");
+    }
+    int rc;
+    if (stale && (rc = prepare_batch(b))) return rc;
+    long long left = nsteps;
+    if (b->timing) {
+        for (; left > 0; --left, ++b->done)
+            if ((rc = batch_phase(b, (int)(b->done & 1)))) return rc;
+    } else {
+        if (b->done & 1) {                       // finish the pair in progress
+            DILBM_CUDA(cudaGraphLaunch(b->g_single[1], b->stream));
+            ++b->done;
+            --left;
+        }
+        for (; left >= 2; left -= 2, b->done += 2) DILBM_CUDA(cudaGraphLaunch(b->g_pair, b->stream));
+        if (left == 1) {
+            DILBM_CUDA(cudaGraphLaunch(b->g_single[0], b->stream));
+            ++b->done;
+        }
+        b->launches += nsteps * batch_launches_per_step(b);
+    }
+    for (size_t k = 0; k < b->members.size(); ++k) {
+        dilbm_ctx *c = b->members[k];
+        c->cur = b->cur0[k] ^ (int)(b->done & 1);
+    }
+    // members' own streams see the batch's work before anything queued later
+    DILBM_CUDA(cudaEventRecord(b->ev_out, b->stream));
+    for (cudaStream_t s : b->member_streams) DILBM_CUDA(cudaStreamWaitEvent(s, b->ev_out, 0));
+    return DILBM_OK;
+}
+
+int dilbm_batch_sync(dilbm_batch *b, int *first_failed) {
+    if (!b) return fail(DILBM_ERR_INVALID_ARG, "NULL batch");
+    DILBM_CUDA(cudaStreamSynchronize(b->stream));
+    if (first_failed) *first_failed = -1;
+    for (size_t k = 0; k < b->members.size(); ++k) {
+        int rc = read_sticky(b->members[k]);
+        if (rc) {
+            if (first_failed) *first_failed = (int)k;
+            return rc;
+        }
+    }
+    return DILBM_OK;
+}
+
+int dilbm_batch_set_timing(dilbm_batch *b, int enable) {
+    if (!b) return fail(DILBM_ERR_INVALID_ARG, "NULL batch");
+    DILBM_CUDA(cudaStreamSynchronize(b->stream));
+    b->timing = enable != 0;
+    b->ev_used = 0;
+    return DILBM_OK;
+}
+
+int dilbm_batch_sweep_time(dilbm_batch *b, double *ms_total, long long *launches) {
+    if (!b || !ms_total || !launches) return fail(DILBM_ERR_INVALID_ARG, "NULL argument");
+    DILBM_CUDA(cudaStreamSynchronize(b->stream));
+    double total = 0.0;
+    for (size_t k = 0; k + 1 < b->ev_used; k += 2) {
+        float ms = 0.f;
+        DILBM_CUDA(cudaEventElapsedTime(&ms, b->ev[k], b->ev[k + 1]));
+        total += ms;
+    }
+    *ms_total = total;
+    *launches = (long long)(b->ev_used / 2);
+    return DILBM_OK;
+}
+
+long long dilbm_batch_launch_count(const dilbm_batch *b) { return b ? b->launches : -1; }
+
+void dilbm_batch_destroy(dilbm_batch *b) {
+    if (!b) return;
+    if (b->stream) cudaStreamSynchronize(b->stream);
+    if (b->g_pair) cudaGraphExecDestroy(b->g_pair);
+    for (int k = 0; k < 2; ++k) {
+        if (b->g_single[k]) cudaGraphExecDestroy(b->g_single[k]);
+        cudaFree(b->part_args[k]);
+    }
+    free_sweep_params(b);
+    cudaFree(b->part_start);
+    for (cudaEvent_t e : b->ev) cudaEventDestroy(e);
+    if (b->ev_in) cudaEventDestroy(b->ev_in);
+    if (b->ev_out) cudaEventDestroy(b->ev_out);
+    if (b->stream) cudaStreamDestroy(b->stream);
+    delete b;
+}
 
 }  // extern "C"

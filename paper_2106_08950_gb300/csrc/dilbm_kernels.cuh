@@ -234,6 +234,62 @@ __device__ __forceinline__ void collide_plain(float d[9], float omega, float drh
     for (int i = 0; i < 9; ++i) d[i] += fmaf(-omega, d[i], X[i]);
 }
 
+// ---- the same collision on two nodes at once, with the paired FP32
+// instructions of sm_100+ (each component rounds exactly as the scalar op).
+__device__ __forceinline__ float2 f2(float a) { return make_float2(a, a); }
+__device__ __forceinline__ float2 add2(float2 a, float2 b) { return __fadd2_rn(a, b); }
+__device__ __forceinline__ float2 sub2(float2 a, float2 b) { return __fadd2_rn(a, make_float2(-b.x, -b.y)); }
+__device__ __forceinline__ float2 mul2(float2 a, float2 b) { return __fmul2_rn(a, b); }
+__device__ __forceinline__ float2 fma2(float2 a, float2 b, float2 c) { return __ffma2_rn(a, b, c); }
+
+__device__ __forceinline__ void moment_form2(float2 m0, float2 Bx, float2 By, float2 Mxx, float2 Myy, float2 Mxy,
+                                             float2 X[9]) {
+    const float2 tr = add2(Mxx, Myy);
+    const float2 S = fma2(f2(-1.5f), tr, m0);
+    const float2 ax = fma2(f2(W1F), S, mul2(f2(0.5f), Mxx)), ay = fma2(f2(W1F), S, mul2(f2(0.5f), Myy));
+    const float2 ap = fma2(f2(W5F), S, mul2(f2(0.125f), fma2(f2(2.0f), Mxy, tr)));
+    const float2 am = fma2(f2(W5F), S, mul2(f2(0.125f), fma2(f2(-2.0f), Mxy, tr)));
+    const float2 bx = mul2(f2(A1F), Bx), by = mul2(f2(A1F), By);
+    const float2 bp = mul2(f2(A5F), add2(Bx, By)), bm = mul2(f2(A5F), sub2(By, Bx));
+    X[0] = fma2(f2(-2.0f), add2(add2(ax, ay), add2(ap, am)), m0);
+    X[1] = add2(ax, bx); X[3] = sub2(ax, bx);
+    X[2] = add2(ay, by); X[4] = sub2(ay, by);
+    X[5] = add2(ap, bp); X[7] = sub2(ap, bp);
+    X[6] = add2(am, bm); X[8] = sub2(am, bm);
+}
+
+__device__ __forceinline__ void relax2(float2 d[9], float2 omega, const float2 X[9]) {
+    const float2 nom = make_float2(-omega.x, -omega.y);
+#pragma unroll
+    for (int i = 0; i < 9; ++i) d[i] = add2(d[i], fma2(nom, d[i], X[i]));
+}
+
+__device__ __forceinline__ void collide_plain2(float2 d[9], float omega, float2 drho, float2 rho, float2 jx,
+                                               float2 jy, float2 ux, float2 uy) {
+    const float2 om = f2(omega);
+    const float2 orho = mul2(om, rho);
+    const float2 rux = mul2(orho, ux);
+    float2 X[9];
+    moment_form2(mul2(om, drho), mul2(om, jx), mul2(om, jy), mul2(rux, ux), mul2(mul2(orho, uy), uy),
+                 mul2(rux, uy), X);
+    relax2(d, om, X);
+}
+
+__device__ __forceinline__ void collide2(float2 d[9], float omega, float2 drho, float2 rho, float2 jx, float2 jy,
+                                         float2 ux, float2 uy, float2 kphi, float2 prho, float2 dux, float2 duy,
+                                         float2 usx, float2 usy, float2 uax, float2 uay) {
+    const float2 om = f2(omega);
+    const float2 orho = mul2(om, rho);
+    const float2 Bx = fma2(om, jx, mul2(prho, dux)), By = fma2(om, jy, mul2(prho, duy));
+    const float2 rux = mul2(orho, ux);
+    const float2 Mxx = fma2(rux, ux, mul2(kphi, mul2(dux, add2(usx, uax))));
+    const float2 Myy = fma2(mul2(orho, uy), uy, mul2(kphi, mul2(duy, add2(usy, uay))));
+    const float2 Mxy = fma2(rux, uy, mul2(kphi, fma2(dux, usy, mul2(uax, duy))));
+    float2 X[9];
+    moment_form2(mul2(om, drho), Bx, By, Mxx, Myy, Mxy, X);
+    relax2(d, om, X);
+}
+
 // Tile ranges along one axis covered by [X - R, X + R] (a disc's bounding
 // interval); periodic intervals wrap and may split in two.  Shared by the
 // binning and the reduction so both visit the same tiles in the same order.
@@ -347,16 +403,14 @@ __device__ __forceinline__ void pull_node_scalar(const T *__restrict__ src, cons
 // Non-equilibrium extrapolation at an edge node (x, y) (Guo et al. 2002, as
 // the paper's Sec. 3 uses): d_b = deq(rho_b, u_b) + d_n - deq(rho_n, u_n),
 // with n the inner neighbour (diagonal at corners; corners take the
-// south/north condition).
-template <typename T>
-__device__ __forceinline__ void edge_extrapolate(const T *__restrict__ src, const Lattice &L, int x, int y, float d[9]) {
-    const int onx = !L.per_x && (x == 0 || x == L.nx - 1);
-    const int ony = !L.per_y && (y == 0 || y == L.ny - 1);
-    const int side = ony ? (y == 0 ? SOUTH : NORTH) : (x == 0 ? WEST : EAST);
-    const int xn = onx ? (x == 0 ? 1 : L.nx - 2) : x;
-    const int yn = ony ? (y == 0 ? 1 : L.ny - 2) : y;
-    float dn[9];
-    pull_node_scalar<T>(src, L, xn, yn, dn);
+// south/north condition).  Kept out of line: few nodes take it, and inlined
+// it would crowd the sweep's instruction cache.
+struct Pop9 {
+    float v[9];
+};
+
+// d_b from the inner neighbour's streamed values dn and the side's condition.
+__device__ __forceinline__ void extrapolate(const Lattice &L, int side, const float dn[9], float out[9]) {
     float drn = 0.f, jx = 0.f, jy = 0.f;
 #pragma unroll
     for (int i = 0; i < 9; ++i) {
@@ -382,7 +436,23 @@ __device__ __forceinline__ void edge_extrapolate(const T *__restrict__ src, cons
     eq_dev9(drb, 1.0f + drb, ubx, uby, eb);
     eq_dev9(drn, rhon, unx, uny, en);
 #pragma unroll
-    for (int i = 0; i < 9; ++i) d[i] = eb[i] + (dn[i] - en[i]);
+    for (int i = 0; i < 9; ++i) out[i] = eb[i] + (dn[i] - en[i]);
+}
+
+// An edge node whose inner neighbour lies on another row (south / north
+// edges and corners): the neighbour's streamed values come from global memory.
+template <typename T>
+__device__ __noinline__ Pop9 edge_values(const T *__restrict__ src, const Lattice &L, int x, int y) {
+    const int onx = !L.per_x && (x == 0 || x == L.nx - 1);
+    const int ony = !L.per_y && (y == 0 || y == L.ny - 1);
+    const int side = ony ? (y == 0 ? SOUTH : NORTH) : (x == 0 ? WEST : EAST);
+    const int xn = onx ? (x == 0 ? 1 : L.nx - 2) : x;
+    const int yn = ony ? (y == 0 ? 1 : L.ny - 2) : y;
+    float dn[9];
+    pull_node_scalar<T>(src, L, xn, yn, dn);
+    Pop9 out;
+    extrapolate(L, side, dn, out.v);
+    return out;
 }
 
 // ------------------------------------------------------------ the sweep
@@ -394,32 +464,397 @@ struct FieldsOut {
     float *rho, *ux, *uy, *phi;   // dense [ny][nx]
 };
 
+// Everything one lattice's sweep needs.
+template <typename T>
+struct SweepArgs {
+    const T *src;               // post-collision populations (GUARD elements in)
+    T *dst;                     // next populations
+    Lattice L;
+    Physics ph;
+    Bins B;                     // this step's bins (counts, ids, records)
+    float4 *partial;            // force / torque partials
+    int *clear;                 // next step's bin counts to zero, or NULL
+    int *err;                   // the lattice's error word
+    FieldsOut fo;               // MODE_FIELDS outputs
+};
+
+// A batched sweep walks one work list over many lattices, their descriptors
+// held in the kernel's parameter space (uniform constant-cache reads, no
+// aliasing with the stores): lattice k owns row segments
+// [item_start[k], item_start[k+1]) and tiles [tile_start[k], tile_start[k+1]).
+constexpr int BATCH_LAUNCH_MAX = 96;     // lattices per batched launch
+
+template <typename T>
+struct BatchArgs {
+    SweepArgs<T> a[BATCH_LAUNCH_MAX];
+    int item_start[BATCH_LAUNCH_MAX + 1];
+    int tile_start[BATCH_LAUNCH_MAX + 1];
+    int n;
+};
+static_assert(sizeof(BatchArgs<float>) <= 32000, "batched sweep parameters exceed the parameter space");
+
+// Particle batches keep their descriptors in device memory: lattice k owns
+// particles [item_start[k], item_start[k+1]).
+struct BatchIndex {
+    const int *item_start;
+    const int *tile_start;
+    int n;
+};
+
+// Largest k with start[k] <= v (start[0] = 0, start ascending, n entries + 1).
+template <typename P>
+__device__ __forceinline__ int batch_find(const P &start, int n, int v) {
+    int lo = 0, hi = n - 1;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (start[mid] <= v) lo = mid; else hi = mid - 1;
+    }
+    return lo;
+}
+
+// Per-warp state of the staging ring.
+struct Ring {
+    uint64_t *bars;
+    uint32_t parity;            // bit s: phase parity the next wait on stage s expects
+    uint32_t pending;           // bit s: stage s has copies in flight
+};
+
+// One row segment (row y, segment tx) of lattice A: wait for its staged rows,
+// hand the stage to the segment `nxt` (row ny2, segment nx2 of lattice An)
+// when there is one, then stream, collide, store and sum the segment's
+// force / torque.  Returns false if the bounded wait gave up.
+template <typename T, int MODE, bool EDGES>
+__device__ __forceinline__ bool sweep_segment(const SweepArgs<T> &A, int y, int tx, T *stage, Ring &ring, int s,
+                                              bool has_next, const SweepArgs<T> &An, int ny2, int nx2,
+                                              float4 *crec, int *cid, int lane) {
+    constexpr int H = halo_of<T>(), SW = segw_of<T>();
+    const Lattice &L = A.L;
+    const Physics &ph = A.ph;
+    const int ty = y / TILE_H, tile = ty * L.ntx + tx;
+    const int tx0 = tx * TILE_W, ty0 = ty * TILE_H;
+    const int x0 = tx0 + lane * VEC;
+
+    // ---- the tile's candidate particles (records written by the binning)
+    __syncwarp();
+    int ncand = A.B.count ? A.B.count[tile] : 0;
+    ncand = ncand > MAXC ? MAXC : ncand;
+    if (lane < ncand) {
+        const long long r = (long long)tile * MAXC + lane;
+#pragma unroll
+        for (int q = 0; q < NREC; ++q) crec[q * MAXC + lane] = A.B.rec[NREC * r + q];
+        cid[lane] = A.B.ids[r];
+    }
+
+    // ---- pull-stream from the staged rows: f_i(x, t+1) = f'_i(x - c_i, t)
+    // a warp-uniform decision: every lane leaves together if any gave up
+    if (!__all_sync(0xffffffffu, mbar_wait_bounded(&ring.bars[s], (ring.parity >> s) & 1u))) return false;
+    ring.parity ^= 1u << s;
+    ring.pending &= ~(1u << s);
+    const int c0 = H + lane * VEC;
+    float d[9][VEC];
+#pragma unroll
+    for (int i = 0; i < 9; ++i) {
+        const float4 v = Storage<T>::lds4(stage + i * SW + c0);
+        if (cxof(i) == 0) {
+            d[i][0] = v.x; d[i][1] = v.y; d[i][2] = v.z; d[i][3] = v.w;
+        } else if (cxof(i) == 1) {
+            d[i][0] = Storage<T>::lds1(stage + i * SW + c0 - 1); d[i][1] = v.x; d[i][2] = v.y; d[i][3] = v.z;
+        } else {
+            d[i][0] = v.y; d[i][1] = v.z; d[i][2] = v.w; d[i][3] = Storage<T>::lds1(stage + i * SW + c0 + VEC);
+        }
+    }
+    __syncwarp();
+    // recycle the stage for the segment STAGES items ahead
+    if (has_next) {
+        fence_proxy_async_smem();
+        issue_segment<T>(An.src, An.L, ny2, nx2, stage, &ring.bars[s], lane);
+        ring.pending |= 1u << s;
+    }
+    // periodic x: the row's first node pulls from column nx-1 and its
+    // last node from column 0, which the staged halo does not hold
+    if (L.per_x && (tx == 0 || tx0 + TILE_W >= L.nx)) {
+#pragma unroll
+        for (int i = 0; i < 9; ++i) {
+            if (cxof(i) == 0) continue;
+            const int sy = wrap_or_clamp(y - cyof(i), L.ny, L.per_y);
+            const T *row = A.src + i * L.plane + (long long)sy * L.pitch;
+            if (cxof(i) == 1 && x0 == 0) d[i][0] = Storage<T>::load1(row + (L.nx - 1));
+            if (cxof(i) == -1) {
+                const int kl = L.nx - 1 - x0;
+#pragma unroll
+                for (int q = 0; q < VEC; ++q)
+                    if (q == kl) d[i][q] = Storage<T>::load1(row);
+            }
+        }
+    }
+    __syncwarp();   // candidate records visible to the whole warp
+
+    // ---- solid fraction (Eq. 14), owner and particle velocity per node:
+    // max over the tile's candidates, lowest particle id on ties
+    float phi[VEC], rxn[VEC], ryn[VEC];
+    int best[VEC], best_id[VEC];
+#pragma unroll
+    for (int q = 0; q < VEC; ++q) { phi[q] = 0.f; rxn[q] = 0.f; ryn[q] = 0.f; best[q] = -1; best_id[q] = 0x7fffffff; }
+    for (int c = 0; c < ncand; ++c) {
+        const float4 ra = crec[c], rb = crec[MAXC + c];
+        const float R = rb.x + ph.cut;
+        float dy = ((float)(y - ty0) - ra.z) - ra.w;
+        if (L.wrap_y) { if (dy >= 0.5f * L.ny) dy -= L.ny; else if (dy < -0.5f * L.ny) dy += L.ny; }
+        const float h2 = R * R - dy * dy;
+        if (h2 < 0.f) continue;                         // this row misses the disc tail
+        const float dx0 = ((float)(x0 - tx0) - ra.x) - ra.y;
+        if (!L.wrap_x) {
+            // the thread's 4 nodes span [dx0, dx0 + 3]
+            const float lo = dx0 > 0.f ? dx0 : (dx0 + (VEC - 1) < 0.f ? -(dx0 + (VEC - 1)) : 0.f);
+            if (lo * lo > h2) continue;
+        }
+        const int id = cid[c];
+#pragma unroll
+        for (int q = 0; q < VEC; ++q) {
+            float dx = dx0 + (float)q;
+            if (L.wrap_x) { if (dx >= 0.5f * L.nx) dx -= L.nx; else if (dx < -0.5f * L.nx) dx += L.nx; }
+            const float d2 = dx * dx + dy * dy;
+            if (d2 > R * R) continue;
+            const float l = rb.x - sqrtf(d2);
+            if (l < -ph.cut) continue;
+            // (1 + tanh(2l/eps)) / 2 == 1 / (1 + exp(-4l/eps))
+            const float pc = 1.0f / (1.0f + expf(-ph.four_over_eps * l));
+            if (pc > phi[q] || (pc == phi[q] && pc > 0.f && id < best_id[q])) {
+                phi[q] = pc; best[q] = c; best_id[q] = id; rxn[q] = dx; ryn[q] = dy;
+            }
+        }
+    }
+
+    const bool row_edge = EDGES && !L.per_y && (y == 0 || y == L.ny - 1);
+    const bool col_edge = EDGES && !L.per_x && (tx == 0 || tx0 + TILE_W >= L.nx);
+    // west / east edge nodes of a row that is not itself an edge row: the
+    // inner neighbour (x + 1 or x - 1, same row) is in this thread's registers
+    // or, for the east edge at the start of a chunk, in the left lane's
+    if (col_edge && !row_edge) {
+        float left[9];
+#pragma unroll
+        for (int i = 0; i < 9; ++i) left[i] = __shfl_up_sync(0xffffffffu, d[i][VEC - 1], 1);
+#pragma unroll
+        for (int q = 0; q < VEC; ++q) {
+            const int x = x0 + q;
+            if (x != 0 && x != L.nx - 1) continue;
+            float dn[9], e[9];
+#pragma unroll
+            for (int i = 0; i < 9; ++i) {
+                if (x == 0) dn[i] = d[i][q < VEC - 1 ? q + 1 : q];            // q == 0 here: x0 == 0
+                else dn[i] = q > 0 ? d[i][q > 0 ? q - 1 : 0] : left[i];
+            }
+            extrapolate(L, x == 0 ? WEST : EAST, dn, e);
+#pragma unroll
+            for (int i = 0; i < 9; ++i) d[i][q] = e[i];
+        }
+    }
+    // warps with no node inside any particle's phi tail collide without the force term
+    const bool coupled = __any_sync(0xffffffffu, max(max(best[0], best[1]), max(best[2], best[3])) >= 0);
+    float acc[VEC][3];
+    bool bad = false;
+
+    // nodes in pairs (2h, 2h + 1) on the paired FP32 instructions
+#pragma unroll
+    for (int h = 0; h < VEC / 2; ++h) {
+        const int qa = 2 * h, qb = 2 * h + 1;
+        float2 dk[9];
+#pragma unroll
+        for (int i = 0; i < 9; ++i) dk[i] = make_float2(d[i][qa], d[i][qb]);
+        if (EDGES && row_edge) {
+            // south / north edge rows (corners included): neighbour on another row
+            if (x0 + qa < L.nx) {
+                const Pop9 e = edge_values<T>(A.src, L, x0 + qa, y);
+#pragma unroll
+                for (int i = 0; i < 9; ++i) dk[i].x = e.v[i];
+            }
+            if (x0 + qb < L.nx) {
+                const Pop9 e = edge_values<T>(A.src, L, x0 + qb, y);
+#pragma unroll
+                for (int i = 0; i < 9; ++i) dk[i].y = e.v[i];
+            }
+        }
+
+        // ---- moments (Eq. 5, Eq. 16)
+        const float2 drho = add2(add2(add2(add2(dk[0], dk[1]), add2(dk[2], dk[3])),
+                                      add2(add2(dk[4], dk[5]), add2(dk[6], dk[7]))), dk[8]);
+        const float2 rho = add2(f2(1.0f), drho);
+        const float2 jx = add2(add2(sub2(dk[1], dk[3]), sub2(dk[5], dk[6])), sub2(dk[8], dk[7]));
+        const float2 jy = sub2(add2(sub2(dk[2], dk[4]), add2(dk[5], dk[6])), add2(dk[7], dk[8]));
+        const float2 inv = make_float2(1.0f / rho.x, 1.0f / rho.y);
+        const float2 ua = mul2(jx, inv), va = mul2(jy, inv);     // u* (Eq. 16)
+        const bool act_a = x0 + qa < L.nx, act_b = x0 + qb < L.nx;
+        if (MODE == MODE_STEP) {
+            if (act_a && (!(rho.x > 0.0f) || !isfinite(ua.x + va.x))) bad = true;
+            if (act_b && (!(rho.y > 0.0f) || !isfinite(ua.y + va.y))) bad = true;
+        }
+        acc[qa][0] = acc[qa][1] = acc[qa][2] = 0.f;
+        acc[qb][0] = acc[qb][1] = acc[qb][2] = 0.f;
+
+        if (!coupled) {
+            if (MODE == MODE_FIELDS) {
+                const long long o = (long long)y * L.nx + x0 + qa;
+                if (act_a) {
+                    if (A.fo.rho) A.fo.rho[o] = rho.x;
+                    if (A.fo.ux) A.fo.ux[o] = ua.x;
+                    if (A.fo.uy) A.fo.uy[o] = va.x;
+                    if (A.fo.phi) A.fo.phi[o] = 0.f;
+                }
+                if (act_b) {
+                    if (A.fo.rho) A.fo.rho[o + 1] = rho.y;
+                    if (A.fo.ux) A.fo.ux[o + 1] = ua.y;
+                    if (A.fo.uy) A.fo.uy[o + 1] = va.y;
+                    if (A.fo.phi) A.fo.phi[o + 1] = 0.f;
+                }
+                continue;
+            }
+            collide_plain2(dk, ph.omega, drho, rho, jx, jy, ua, va);
+        } else {
+            // u_s - u* from the particle velocity carried as FP32 hi + lo:
+            // u_s = U + omega x r with r the node's offset from the centre
+            float du[2] = {0.f, 0.f}, dv[2] = {0.f, 0.f};
+            const float uas[2] = {ua.x, ua.y}, vas[2] = {va.x, va.y};
+#pragma unroll
+            for (int m = 0; m < 2; ++m) {
+                const int q = qa + m;
+                const int b = best[q];
+                if (b >= 0) {
+                    const float4 rb = crec[MAXC + b], rl = crec[2 * MAXC + b];
+                    du[m] = fmaf(-rb.w, ryn[q], rb.y - uas[m]) + fmaf(-rl.z, ryn[q], rl.x);
+                    dv[m] = fmaf(rb.w, rxn[q], rb.z - vas[m]) + fmaf(rl.z, rxn[q], rl.y);
+                }
+            }
+            const float2 dux = make_float2(du[0], du[1]), duy = make_float2(dv[0], dv[1]);
+            const float2 usx = add2(ua, dux), usy = add2(va, duy);
+            const float2 phq = make_float2(phi[qa], phi[qb]);
+            // ---- corrected velocity (Eq. 17)
+            const float2 hph = mul2(f2(0.5f), phq);
+            const float2 ux = fma2(hph, dux, ua), uy = fma2(hph, duy, va);
+
+            if (MODE == MODE_FIELDS) {
+                const long long o = (long long)y * L.nx + x0 + qa;
+                if (act_a) {
+                    if (A.fo.rho) A.fo.rho[o] = rho.x;
+                    if (A.fo.ux) A.fo.ux[o] = ux.x;
+                    if (A.fo.uy) A.fo.uy[o] = uy.x;
+                    if (A.fo.phi) A.fo.phi[o] = phq.x;
+                }
+                if (act_b) {
+                    if (A.fo.rho) A.fo.rho[o + 1] = rho.y;
+                    if (A.fo.ux) A.fo.ux[o + 1] = ux.y;
+                    if (A.fo.uy) A.fo.uy[o + 1] = uy.y;
+                    if (A.fo.phi) A.fo.phi[o + 1] = phq.y;
+                }
+                continue;
+            }
+            const float2 prho = mul2(rho, phq);
+            collide2(dk, ph.omega, drho, rho, jx, jy, ux, uy, mul2(f2(ph.kf), prho), prho, dux, duy, usx, usy, ua,
+                     va);
+
+            // ---- Eqs. 18-19 per node, by the closed form sum_i F_i c_i = kf rho (u_s - u*)
+#pragma unroll
+            for (int m = 0; m < 2; ++m) {
+                const int q = qa + m;
+                if (x0 + q < L.nx && best[q] >= 0) {
+                    const float sg = -(m ? prho.y : prho.x) * ph.kforce;
+                    const float gx = sg * du[m], gy = sg * dv[m];
+                    acc[q][0] = gx; acc[q][1] = gy; acc[q][2] = rxn[q] * gy - ryn[q] * gx;
+                }
+            }
+        }
+#pragma unroll
+        for (int i = 0; i < 9; ++i) {
+            d[i][qa] = dk[i].x;
+            d[i][qb] = dk[i].y;
+        }
+    }
+
+    if (MODE == MODE_FIELDS) return true;
+    if (__any_sync(0xffffffffu, bad) && lane == 0) atomicOr(A.err, ERR_UNSTABLE);
+
+    // ---- store the collided populations
+    {
+        const bool full = x0 + VEC <= L.nx;
+#pragma unroll
+        for (int i = 0; i < 9; ++i) {
+            T *row = A.dst + i * L.plane + (long long)y * L.pitch;
+            if (full) {
+                Storage<T>::store4(row + x0, make_float4(d[i][0], d[i][1], d[i][2], d[i][3]));
+            } else {
+#pragma unroll
+                for (int q = 0; q < VEC; ++q)
+                    if (x0 + q < L.nx) Storage<T>::store1(row + x0 + q, d[i][q]);
+            }
+        }
+    }
+
+    // ---- this row segment's force / torque per candidate (fixed shuffle tree)
+    for (int c = 0; c < ncand; ++c) {
+        if (!coupled) {
+            if (lane == 0)
+                A.partial[((long long)tile * MAXC + c) * TILE_H + (y - ty0)] = make_float4(0.f, 0.f, 0.f, 0.f);
+            continue;
+        }
+        float v0 = 0.f, v1 = 0.f, v2 = 0.f;
+#pragma unroll
+        for (int q = 0; q < VEC; ++q)
+            if (best[q] == c) { v0 += acc[q][0]; v1 += acc[q][1]; v2 += acc[q][2]; }
+        if (__any_sync(0xffffffffu, v0 != 0.f || v1 != 0.f || v2 != 0.f)) {
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) {
+                v0 += __shfl_xor_sync(0xffffffffu, v0, o);
+                v1 += __shfl_xor_sync(0xffffffffu, v1, o);
+                v2 += __shfl_xor_sync(0xffffffffu, v2, o);
+            }
+        }
+        if (lane == 0)
+            A.partial[((long long)tile * MAXC + c) * TILE_H + (y - ty0)] = make_float4(v0, v1, v2, 0.f);
+    }
+    return true;
+}
+
+// Shared-memory carve-up common to both sweep kernels.
+template <typename T>
+struct SweepSmem {
+    T *stages;
+    float4 *crec;
+    int *cid;
+    uint64_t *bars;
+    __device__ __forceinline__ SweepSmem(unsigned char *raw, int warp) {
+        constexpr int SW = segw_of<T>();
+        constexpr size_t STAGE_BYTES = (size_t)SWEEP_WARPS * STAGES * 9 * SW * sizeof(T);
+        constexpr size_t REC_BYTES = (size_t)SWEEP_WARPS * NREC * MAXC * sizeof(float4);
+        constexpr size_t ID_BYTES = (size_t)SWEEP_WARPS * MAXC * sizeof(int);
+        stages = reinterpret_cast<T *>(raw) + (size_t)warp * STAGES * 9 * SW;
+        crec = reinterpret_cast<float4 *>(raw + STAGE_BYTES) + (size_t)warp * NREC * MAXC;
+        cid = reinterpret_cast<int *>(raw + STAGE_BYTES + REC_BYTES) + warp * MAXC;
+        bars = reinterpret_cast<uint64_t *>(raw + STAGE_BYTES + REC_BYTES + ID_BYTES) + warp * STAGES;
+    }
+};
+
+// The sweep over one lattice.  Persistent: warps take row segments
+// round-robin (neighbouring warps on neighbouring segments); each warp keeps
+// STAGES segments staged ahead.
 template <typename T, int MODE, bool EDGES>
 __global__ void __launch_bounds__(SWEEP_WARPS * 32, 2)
-sweep_kernel(const T *__restrict__ src, T *__restrict__ dst, Lattice L, Physics ph,
-             Bins B, float4 *__restrict__ partial, int *__restrict__ clear_count, FieldsOut fo,
-             int *__restrict__ err)
+sweep_kernel(const __grid_constant__ SweepArgs<T> one)
 {
-    constexpr int H = halo_of<T>(), SW = segw_of<T>();
-    constexpr size_t STAGE_BYTES = (size_t)SWEEP_WARPS * STAGES * 9 * SW * sizeof(T);
-    constexpr size_t REC_BYTES = (size_t)SWEEP_WARPS * NREC * MAXC * sizeof(float4);
-    constexpr size_t ID_BYTES = (size_t)SWEEP_WARPS * MAXC * sizeof(int);
+    constexpr int SW = segw_of<T>();
     extern __shared__ __align__(128) unsigned char smem_raw[];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    T *const stages = reinterpret_cast<T *>(smem_raw) + (size_t)warp * STAGES * 9 * SW;
-    float4 *const crec = reinterpret_cast<float4 *>(smem_raw + STAGE_BYTES) + (size_t)warp * NREC * MAXC;
-    int *const cid = reinterpret_cast<int *>(smem_raw + STAGE_BYTES + REC_BYTES) + warp * MAXC;
-    uint64_t *const bars = reinterpret_cast<uint64_t *>(smem_raw + STAGE_BYTES + REC_BYTES + ID_BYTES) + warp * STAGES;
-
+    SweepSmem<T> sm(smem_raw, warp);
+    Ring ring;
+    ring.bars = sm.bars;
     if (lane == 0) {
-        for (int s = 0; s < STAGES; ++s) mbar_init(&bars[s], 1);
+        for (int s = 0; s < STAGES; ++s) mbar_init(&ring.bars[s], 1);
         mbar_fence_init();
     }
     __syncwarp();
+    const Lattice &L = one.L;
     // the next step's bins start empty (nothing reads them during this sweep)
-    if (clear_count)
+    if (one.clear)
         for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < L.ntx * L.nty; t += gridDim.x * blockDim.x)
-            clear_count[t] = 0;
+            one.clear[t] = 0;
 
     const int nitems = L.ny * L.ntx;
     const int gw = blockIdx.x * SWEEP_WARPS + warp, nw = gridDim.x * SWEEP_WARPS;
@@ -431,254 +866,126 @@ sweep_kernel(const T *__restrict__ src, T *__restrict__ dst, Lattice L, Physics 
         if (xx >= L.ntx) { xx -= L.ntx; ++yy; }
     };
     int y = gw / L.ntx, tx = gw - (gw / L.ntx) * L.ntx;
+    ring.parity = 0;
+    ring.pending = 0;
     {
         int py = y, ptx = tx;
         for (int s = 0; s < STAGES; ++s) {
-            if (gw + s * nw < nitems) issue_segment<T>(src, L, py, ptx, stages + s * 9 * SW, &bars[s], lane);
+            if (gw + s * nw < nitems) {
+                issue_segment<T>(one.src, L, py, ptx, sm.stages + s * 9 * SW, &ring.bars[s], lane);
+                ring.pending |= 1u << s;
+            }
             advance(py, ptx);
         }
     }
+    // (row, segment) STAGES items ahead, for the stage being recycled
+    int ay = y, atx = tx;
+    for (int s = 0; s < STAGES; ++s) advance(ay, atx);
 
-    uint32_t parity = 0;     // bit s: phase parity the next wait on stage s expects
-    uint32_t pending = 0;    // bit s: stage s has copies in flight
-    for (int s = 0; s < STAGES; ++s)
-        if (gw + s * nw < nitems) pending |= 1u << s;
-    bool bad = false, timed_out = false;
     int k = 0;
+    bool timed_out = false;
     for (int item = gw; item < nitems; item += nw, ++k) {
-        if (k > 0) advance(y, tx);
+        if (k > 0) {
+            advance(y, tx);
+            advance(ay, atx);
+        }
         const int s = k % STAGES;
-        const int ty = y / TILE_H, tile = ty * L.ntx + tx;
-        const int tx0 = tx * TILE_W, ty0 = ty * TILE_H;
-        const int x0 = tx0 + lane * VEC;
-
-        // ---- the tile's candidate particles (records written by the binning)
-        __syncwarp();
-        int ncand = B.count ? B.count[tile] : 0;
-        ncand = ncand > MAXC ? MAXC : ncand;
-        if (lane < ncand) {
-            const long long r = (long long)tile * MAXC + lane;
-#pragma unroll
-            for (int q = 0; q < NREC; ++q) crec[q * MAXC + lane] = B.rec[NREC * r + q];
-            cid[lane] = B.ids[r];
-        }
-
-        // ---- pull-stream from the staged rows: f_i(x, t+1) = f'_i(x - c_i, t)
-        // a warp-uniform decision: every lane leaves together if any gave up
-        if (!__all_sync(0xffffffffu, mbar_wait_bounded(&bars[s], (parity >> s) & 1u))) { timed_out = true; break; }
-        parity ^= 1u << s;
-        pending &= ~(1u << s);
-        const T *st = stages + s * 9 * SW;
-        const int c0 = H + lane * VEC;
-        float d[9][VEC];
-#pragma unroll
-        for (int i = 0; i < 9; ++i) {
-            const float4 v = Storage<T>::lds4(st + i * SW + c0);
-            if (cxof(i) == 0) {
-                d[i][0] = v.x; d[i][1] = v.y; d[i][2] = v.z; d[i][3] = v.w;
-            } else if (cxof(i) == 1) {
-                d[i][0] = Storage<T>::lds1(st + i * SW + c0 - 1); d[i][1] = v.x; d[i][2] = v.y; d[i][3] = v.z;
-            } else {
-                d[i][0] = v.y; d[i][1] = v.z; d[i][2] = v.w; d[i][3] = Storage<T>::lds1(st + i * SW + c0 + VEC);
-            }
-        }
-        __syncwarp();
-        // recycle the stage for the segment STAGES items ahead
-        {
-            const int nxt = item + STAGES * nw;
-            if (nxt < nitems) {
-                int ny2 = y, nx2 = tx;
-                for (int q = 0; q < STAGES; ++q) advance(ny2, nx2);
-                fence_proxy_async_smem();
-                issue_segment<T>(src, L, ny2, nx2, stages + s * 9 * SW, &bars[s], lane);
-                pending |= 1u << s;
-            }
-        }
-        // periodic x: the row's first node pulls from column nx-1 and its
-        // last node from column 0, which the staged halo does not hold
-        if (L.per_x && (tx == 0 || tx0 + TILE_W >= L.nx)) {
-#pragma unroll
-            for (int i = 0; i < 9; ++i) {
-                if (cxof(i) == 0) continue;
-                const int sy = wrap_or_clamp(y - cyof(i), L.ny, L.per_y);
-                const T *row = src + i * L.plane + (long long)sy * L.pitch;
-                if (cxof(i) == 1 && x0 == 0) d[i][0] = Storage<T>::load1(row + (L.nx - 1));
-                if (cxof(i) == -1) {
-                    const int kl = L.nx - 1 - x0;
-#pragma unroll
-                    for (int q = 0; q < VEC; ++q)
-                        if (q == kl) d[i][q] = Storage<T>::load1(row);
-                }
-            }
-        }
-        __syncwarp();   // candidate records visible to the whole warp
-
-        // ---- solid fraction (Eq. 14), owner and particle velocity per node:
-        // max over the tile's candidates, lowest particle id on ties
-        float phi[VEC], rxn[VEC], ryn[VEC];
-        int best[VEC], best_id[VEC];
-#pragma unroll
-        for (int q = 0; q < VEC; ++q) { phi[q] = 0.f; rxn[q] = 0.f; ryn[q] = 0.f; best[q] = -1; best_id[q] = 0x7fffffff; }
-        for (int c = 0; c < ncand; ++c) {
-            const float4 ra = crec[c], rb = crec[MAXC + c];
-            const float R = rb.x + ph.cut;
-            float dy = ((float)(y - ty0) - ra.z) - ra.w;
-            if (L.wrap_y) { if (dy >= 0.5f * L.ny) dy -= L.ny; else if (dy < -0.5f * L.ny) dy += L.ny; }
-            const float h2 = R * R - dy * dy;
-            if (h2 < 0.f) continue;                         // this row misses the disc tail
-            const float dx0 = ((float)(x0 - tx0) - ra.x) - ra.y;
-            if (!L.wrap_x) {
-                // the thread's 4 nodes span [dx0, dx0 + 3]
-                const float lo = dx0 > 0.f ? dx0 : (dx0 + (VEC - 1) < 0.f ? -(dx0 + (VEC - 1)) : 0.f);
-                if (lo * lo > h2) continue;
-            }
-            const int id = cid[c];
-#pragma unroll
-            for (int q = 0; q < VEC; ++q) {
-                float dx = dx0 + (float)q;
-                if (L.wrap_x) { if (dx >= 0.5f * L.nx) dx -= L.nx; else if (dx < -0.5f * L.nx) dx += L.nx; }
-                const float d2 = dx * dx + dy * dy;
-                if (d2 > R * R) continue;
-                const float l = rb.x - sqrtf(d2);
-                if (l < -ph.cut) continue;
-                // (1 + tanh(2l/eps)) / 2 == 1 / (1 + exp(-4l/eps))
-                const float pc = 1.0f / (1.0f + expf(-ph.four_over_eps * l));
-                if (pc > phi[q] || (pc == phi[q] && pc > 0.f && id < best_id[q])) {
-                    phi[q] = pc; best[q] = c; best_id[q] = id; rxn[q] = dx; ryn[q] = dy;
-                }
-            }
-        }
-
-        const bool row_edge = EDGES && !L.per_y && (y == 0 || y == L.ny - 1);
-        const bool col_edge = EDGES && !L.per_x && (tx == 0 || tx0 + TILE_W >= L.nx);
-        // warps with no node inside any particle's phi tail collide without the force term
-        const bool coupled = __any_sync(0xffffffffu, max(max(best[0], best[1]), max(best[2], best[3])) >= 0);
-        float acc[VEC][3];
-
-#pragma unroll
-        for (int q = 0; q < VEC; ++q) {
-            const int x = x0 + q;
-            const bool active = x < L.nx;
-            acc[q][0] = acc[q][1] = acc[q][2] = 0.f;
-            float dk[9];
-#pragma unroll
-            for (int i = 0; i < 9; ++i) dk[i] = d[i][q];
-            if (EDGES && (row_edge || col_edge) && active) {
-                const bool onx = !L.per_x && (x == 0 || x == L.nx - 1);
-                if (row_edge || onx) edge_extrapolate<T>(src, L, x, y, dk);
-            }
-
-            // ---- moments (Eq. 5, Eq. 16)
-            const float drho = ((dk[0] + dk[1]) + (dk[2] + dk[3])) + ((dk[4] + dk[5]) + (dk[6] + dk[7])) + dk[8];
-            const float rho = 1.0f + drho;
-            const float jx = (dk[1] - dk[3]) + (dk[5] - dk[6]) + (dk[8] - dk[7]);
-            const float jy = (dk[2] - dk[4]) + (dk[5] + dk[6]) - (dk[7] + dk[8]);
-            const float inv = 1.0f / rho;
-            const float uax = jx * inv, uay = jy * inv;
-            if (MODE == MODE_STEP && active && (!(rho > 0.0f) || !isfinite(uax + uay))) bad = true;
-
-            if (!coupled) {
-                if (MODE == MODE_FIELDS) {
-                    if (active) {
-                        const long long o = (long long)y * L.nx + x;
-                        if (fo.rho) fo.rho[o] = rho;
-                        if (fo.ux) fo.ux[o] = uax;
-                        if (fo.uy) fo.uy[o] = uay;
-                        if (fo.phi) fo.phi[o] = 0.f;
-                    }
-                    continue;
-                }
-                collide_plain(dk, ph.omega, drho, rho, jx, jy, uax, uay);
-            } else {
-                // u_s - u* from the particle velocity carried as FP32 hi + lo:
-                // u_s = U + omega x r with r the node's offset from the centre
-                float dux = 0.f, duy = 0.f;
-                const int b = best[q];
-                if (b >= 0) {
-                    const float4 rb = crec[MAXC + b], rl = crec[2 * MAXC + b];
-                    dux = fmaf(-rb.w, ryn[q], rb.y - uax) + fmaf(-rl.z, ryn[q], rl.x);
-                    duy = fmaf(rb.w, rxn[q], rb.z - uay) + fmaf(rl.z, rxn[q], rl.y);
-                }
-                const float usx = uax + dux, usy = uay + duy;
-                const float ph_q = phi[q];
-                // ---- corrected velocity (Eq. 17)
-                const float ux = fmaf(0.5f * ph_q, dux, uax), uy = fmaf(0.5f * ph_q, duy, uay);
-
-                if (MODE == MODE_FIELDS) {
-                    if (active) {
-                        const long long o = (long long)y * L.nx + x;
-                        if (fo.rho) fo.rho[o] = rho;
-                        if (fo.ux) fo.ux[o] = ux;
-                        if (fo.uy) fo.uy[o] = uy;
-                        if (fo.phi) fo.phi[o] = ph_q;
-                    }
-                    continue;
-                }
-                collide(dk, ph.omega, drho, rho, jx, jy, ux, uy, ph.kf * rho * ph_q, rho * ph_q, dux, duy, usx, usy,
-                        uax, uay);
-
-                // ---- Eqs. 18-19 per node, by the closed form sum_i F_i c_i = kf rho (u_s - u*)
-                if (active && b >= 0) {
-                    const float sg = -ph_q * ph.kforce * rho;
-                    const float gx = sg * dux, gy = sg * duy;
-                    acc[q][0] = gx; acc[q][1] = gy; acc[q][2] = rxn[q] * gy - ryn[q] * gx;
-                }
-            }
-#pragma unroll
-            for (int i = 0; i < 9; ++i) d[i][q] = dk[i];
-        }
-
-        if (MODE == MODE_FIELDS) continue;
-
-        // ---- store the collided populations
-        {
-            const bool full = x0 + VEC <= L.nx;
-#pragma unroll
-            for (int i = 0; i < 9; ++i) {
-                T *row = dst + i * L.plane + (long long)y * L.pitch;
-                if (full) {
-                    Storage<T>::store4(row + x0, make_float4(d[i][0], d[i][1], d[i][2], d[i][3]));
-                } else {
-#pragma unroll
-                    for (int q = 0; q < VEC; ++q)
-                        if (x0 + q < L.nx) Storage<T>::store1(row + x0 + q, d[i][q]);
-                }
-            }
-        }
-
-        // ---- this row segment's force / torque per candidate (fixed shuffle tree)
-        for (int c = 0; c < ncand; ++c) {
-            if (!coupled) {
-                if (lane == 0)
-                    partial[((long long)tile * MAXC + c) * TILE_H + (y - ty0)] = make_float4(0.f, 0.f, 0.f, 0.f);
-                continue;
-            }
-            float v0 = 0.f, v1 = 0.f, v2 = 0.f;
-#pragma unroll
-            for (int q = 0; q < VEC; ++q)
-                if (best[q] == c) { v0 += acc[q][0]; v1 += acc[q][1]; v2 += acc[q][2]; }
-            if (__any_sync(0xffffffffu, v0 != 0.f || v1 != 0.f || v2 != 0.f)) {
-#pragma unroll
-                for (int o = 16; o > 0; o >>= 1) {
-                    v0 += __shfl_xor_sync(0xffffffffu, v0, o);
-                    v1 += __shfl_xor_sync(0xffffffffu, v1, o);
-                    v2 += __shfl_xor_sync(0xffffffffu, v2, o);
-                }
-            }
-            if (lane == 0)
-                partial[((long long)tile * MAXC + c) * TILE_H + (y - ty0)] = make_float4(v0, v1, v2, 0.f);
+        const bool has_next = item + STAGES * nw < nitems;
+        if (!sweep_segment<T, MODE, EDGES>(one, y, tx, sm.stages + s * 9 * SW, ring, s, has_next, one, ay, atx,
+                                           sm.crec, sm.cid, lane)) {
+            timed_out = true;
+            break;
         }
     }
-
     if (timed_out) {
-        if (lane == 0) atomicOr(err, ERR_TIMEOUT);
+        if (lane == 0) atomicOr(one.err, ERR_TIMEOUT);
         // let the copies this warp still has in flight land before the block
         // releases its shared memory (each wait bounded again)
         for (int s = 0; s < STAGES; ++s)
-            if (pending & (1u << s)) mbar_wait_bounded(&bars[s], (parity >> s) & 1u);
-        return;
+            if (ring.pending & (1u << s)) mbar_wait_bounded(&ring.bars[s], (ring.parity >> s) & 1u);
     }
-    if (MODE == MODE_STEP && __any_sync(0xffffffffu, bad) && lane == 0) atomicOr(err, ERR_UNSTABLE);
+}
+
+// Position in a batched work list: item, its lattice, row and segment.
+struct Cursor {
+    int item, lat, y, tx;
+};
+
+template <typename T>
+__device__ __forceinline__ void cursor_seek(const BatchArgs<T> &ba, Cursor &c, int item) {
+    c.item = item;
+    c.lat = batch_find(ba.item_start, ba.n, item);
+    const int local = item - ba.item_start[c.lat];
+    const int ntx = ba.a[c.lat].L.ntx;
+    c.y = local / ntx;
+    c.tx = local - c.y * ntx;
+}
+
+// The sweep over a batch of lattices (at most BATCH_LAUNCH_MAX per launch).
+// Warps take the concatenated row segments round-robin, as in the
+// single-lattice sweep, so that neighbouring warps stage neighbouring rows
+// (DRAM page locality); each item finds its lattice by a binary search in the
+// parameter space.
+template <typename T, int MODE>
+__global__ void __launch_bounds__(SWEEP_WARPS * 32, 2)
+sweep_batch_kernel(const __grid_constant__ BatchArgs<T> ba)
+{
+    constexpr int SW = segw_of<T>();
+    extern __shared__ __align__(128) unsigned char smem_raw[];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    SweepSmem<T> sm(smem_raw, warp);
+    Ring ring;
+    ring.bars = sm.bars;
+    if (lane == 0) {
+        for (int s = 0; s < STAGES; ++s) mbar_init(&ring.bars[s], 1);
+        mbar_fence_init();
+    }
+    __syncwarp();
+    {
+        const int ntiles = ba.tile_start[ba.n];
+        for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < ntiles; t += gridDim.x * blockDim.x) {
+            const int lat = batch_find(ba.tile_start, ba.n, t);
+            if (ba.a[lat].clear) ba.a[lat].clear[t - ba.tile_start[lat]] = 0;
+        }
+    }
+
+    const int nitems = ba.item_start[ba.n];
+    const int gw = blockIdx.x * SWEEP_WARPS + warp, nw = gridDim.x * SWEEP_WARPS;
+    Cursor cur, ahead;
+    ring.parity = 0;
+    ring.pending = 0;
+    for (int s = 0; s < STAGES; ++s) {
+        const int it = gw + s * nw;
+        if (it < nitems) {
+            cursor_seek(ba, ahead, it);
+            issue_segment<T>(ba.a[ahead.lat].src, ba.a[ahead.lat].L, ahead.y, ahead.tx, sm.stages + s * 9 * SW,
+                             &ring.bars[s], lane);
+            ring.pending |= 1u << s;
+        }
+    }
+
+    int k = 0;
+    bool timed_out = false;
+    int last_lat = 0;
+    for (int item = gw; item < nitems; item += nw, ++k) {
+        const int s = k % STAGES;
+        cursor_seek(ba, cur, item);
+        last_lat = cur.lat;
+        const int nxt = item + STAGES * nw;
+        const bool has_next = nxt < nitems;
+        if (has_next) cursor_seek(ba, ahead, nxt);
+        const int nlat = has_next ? ahead.lat : cur.lat;
+        if (!sweep_segment<T, MODE, true>(ba.a[cur.lat], cur.y, cur.tx, sm.stages + s * 9 * SW, ring, s, has_next,
+                                          ba.a[nlat], ahead.y, ahead.tx, sm.crec, sm.cid, lane)) {
+            timed_out = true;
+            break;
+        }
+    }
+    if (timed_out) {
+        if (lane == 0) atomicOr(ba.a[last_lat].err, ERR_TIMEOUT);
+        for (int s = 0; s < STAGES; ++s)
+            if (ring.pending & (1u << s)) mbar_wait_bounded(&ring.bars[s], (ring.parity >> s) & 1u);
+    }
 }
 
 // ------------------------------------------------------------ particles
@@ -700,7 +1007,7 @@ __device__ __forceinline__ int range_len(const AxisTiles &a) {
     return n;
 }
 
-// One warp per particle.  With integrate != 0:
+// One particle, by one warp.  With integrate != 0:
 //   1. hydrodynamic force and torque (Eqs. 18-19): the row-segment partials of
 //      the tiles the particle was binned into, summed in FP64 in a fixed
 //      order (lanes take fixed (tile, row) entries, then a fixed shuffle tree);
@@ -712,13 +1019,31 @@ __device__ __forceinline__ int range_len(const AxisTiles &a) {
 // reaches (lanes take the tiles in a fixed order), with the record the sweep
 // reads: the centre relative to the tile origin (minimum image about the tile
 // centre) as FP32 hi + lo, radius and velocities.
-static __global__ void particles_kernel(Lattice L, Physics ph, Particles P, BodyParams bp, Bins bin_in, Bins bin_out,
-                                 const float4 *__restrict__ partial, int pin, int pout, int integrate,
-                                 double *__restrict__ force, double *__restrict__ fcol, int *__restrict__ err)
-{
-    const int lane = threadIdx.x & 31;
-    const int p = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-    if (p >= bp.np) return;
+// Everything one lattice's particle update needs.
+struct PartArgs {
+    Lattice L;
+    Physics ph;
+    Particles P;
+    BodyParams bp;
+    Bins bin_in, bin_out;       // bins the sweep used / bins for the next sweep
+    const float4 *partial;
+    int pin, pout;              // position copy read / written
+    int integrate;
+    double *force, *fcol;
+    int *err;
+};
+
+__device__ __forceinline__ void particle_body(const PartArgs &A, int p, int lane) {
+    const Lattice &L = A.L;
+    const Physics &ph = A.ph;
+    const Particles &P = A.P;
+    const BodyParams &bp = A.bp;
+    const Bins &bin_in = A.bin_in, &bin_out = A.bin_out;
+    const float4 *__restrict__ partial = A.partial;
+    const int pin = A.pin, pout = A.pout, integrate = A.integrate;
+    double *__restrict__ force = A.force;
+    double *__restrict__ fcol = A.fcol;
+    int *__restrict__ err = A.err;
     // pick the position copies without indexing the parameter arrays
     const double *xin = pin ? P.x[1] : P.x[0], *yin = pin ? P.y[1] : P.y[0];
     const float *xfin = pin ? P.xf[1] : P.xf[0], *yfin = pin ? P.yf[1] : P.yf[0];
@@ -890,6 +1215,22 @@ static __global__ void particles_kernel(Lattice L, Physics ph, Particles P, Body
         bin_out.pslot[(long long)p * MAXT + k] = entry;
     }
     if (lane == 0) bin_out.npslot[p] = total;
+}
+
+// One warp per particle of one lattice (BATCH = false) or of every lattice of
+// a batch (BATCH = true; bi.item_start holds each lattice's first particle).
+template <bool BATCH>
+__global__ void particles_kernel(const __grid_constant__ PartArgs one, const PartArgs *__restrict__ many, BatchIndex bi) {
+    const int lane = threadIdx.x & 31;
+    const int gwp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    if constexpr (BATCH) {
+        if (gwp >= bi.item_start[bi.n]) return;
+        const int lat = batch_find(bi.item_start, bi.n, gwp);
+        particle_body(many[lat], gwp - bi.item_start[lat], lane);
+    } else {
+        if (gwp >= one.bp.np) return;
+        particle_body(one, gwp, lane);
+    }
 }
 
 // ------------------------------------------------------------ conversions

@@ -203,12 +203,29 @@ extern "C" int dilbm_step_static(const dilbm_grid *g, double tau, double interfa
     S_CUDA(cudaMemsetAsync(bins[0].count, 0, sizeof(int) * 2 * S_MAX_TILES, st));
     S_CUDA(cudaMemsetAsync(err, 0, sizeof(int), st));
 
+    auto part_args = [&](int pin, int pout, int integrate, const Bins &bin_in, const Bins &bin_out) {
+        PartArgs a{};
+        a.L = L;
+        a.ph = ph;
+        a.P = P;
+        a.bp = bp;
+        a.bin_in = bin_in;
+        a.bin_out = bin_out;
+        a.partial = partial;
+        a.pin = pin;
+        a.pout = pout;
+        a.integrate = integrate;
+        a.force = force;
+        a.fcol = fcol;
+        a.err = err;
+        return a;
+    };
     if (np > 0) {
         particles_in_kernel<<<(np + 127) / 128, 128, 0, st>>>(particles, P, np, L.nx, L.ny, L.per_x, L.per_y, err);
         S_CUDA(cudaGetLastError());
         // bin the particles where they are (positions copy 0, bins 0)
-        particles_kernel<<<(np * 32 + 127) / 128, 128, 0, st>>>(L, ph, P, bp, bins[0], bins[0], partial, 0, 0, 0,
-                                                               force, fcol, err);
+        particles_kernel<false><<<(np * 32 + 127) / 128, 128, 0, st>>>(part_args(0, 0, 0, bins[0], bins[0]),
+                                                                       nullptr, BatchIndex{});
         S_CUDA(cudaGetLastError());
     }
 
@@ -221,26 +238,30 @@ extern "C" int dilbm_step_static(const dilbm_grid *g, double tau, double interfa
     long long blocks = 2LL * sms;
     const long long need = (items + SWEEP_WARPS - 1) / SWEEP_WARPS;
     if (blocks > need) blocks = need;
-    const float *src = f_in + GUARD;
-    float *dst = f_out + GUARD;
-    int *clear = np > 0 ? bins[1].count : nullptr;
+    SweepArgs<float> sa{};
+    sa.src = f_in + GUARD;
+    sa.dst = f_out + GUARD;
+    sa.L = L;
+    sa.ph = ph;
+    sa.B = bins[0];
+    sa.partial = partial;
+    sa.clear = np > 0 ? bins[1].count : nullptr;
+    sa.err = err;
     if (L.per_x && L.per_y) {
         S_CUDA(cudaFuncSetAttribute(sweep_kernel<float, MODE_STEP, false>,
                                     cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-        sweep_kernel<float, MODE_STEP, false><<<(unsigned)blocks, SWEEP_WARPS * 32, smem, st>>>(
-            src, dst, L, ph, bins[0], partial, clear, FieldsOut{}, err);
+        sweep_kernel<float, MODE_STEP, false><<<(unsigned)blocks, SWEEP_WARPS * 32, smem, st>>>(sa);
     } else {
         S_CUDA(cudaFuncSetAttribute(sweep_kernel<float, MODE_STEP, true>,
                                     cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-        sweep_kernel<float, MODE_STEP, true><<<(unsigned)blocks, SWEEP_WARPS * 32, smem, st>>>(
-            src, dst, L, ph, bins[0], partial, clear, FieldsOut{}, err);
+        sweep_kernel<float, MODE_STEP, true><<<(unsigned)blocks, SWEEP_WARPS * 32, smem, st>>>(sa);
     }
     S_CUDA(cudaGetLastError());
 
     if (np > 0) {
         // force reduction, Wan-Turek, Newton-Euler (positions copy 0 -> 1)
-        particles_kernel<<<(np * 32 + 127) / 128, 128, 0, st>>>(L, ph, P, bp, bins[0], bins[1], partial, 0, 1, 1,
-                                                               force, fcol, err);
+        particles_kernel<false><<<(np * 32 + 127) / 128, 128, 0, st>>>(part_args(0, 1, 1, bins[0], bins[1]),
+                                                                       nullptr, BatchIndex{});
         S_CUDA(cudaGetLastError());
         particles_out_kernel<<<(np + 127) / 128, 128, 0, st>>>(particles, P, np);
         S_CUDA(cudaGetLastError());

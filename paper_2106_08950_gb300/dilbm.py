@@ -89,9 +89,19 @@ def load_library(path: Optional[str] = None):
     L.dilbm_sweep_time.argtypes = [vp, dp, C.POINTER(C.c_longlong)]
     L.dilbm_launch_count.argtypes = [vp]
     L.dilbm_launch_count.restype = C.c_longlong
+    L.dilbm_batch_create.argtypes = [C.POINTER(vp), ip, vp, C.POINTER(vp)]
+    L.dilbm_batch_step.argtypes = [vp, C.c_longlong]
+    L.dilbm_batch_sync.argtypes = [vp, C.POINTER(C.c_int)]
+    L.dilbm_batch_set_timing.argtypes = [vp, ip]
+    L.dilbm_batch_sweep_time.argtypes = [vp, dp, C.POINTER(C.c_longlong)]
+    L.dilbm_batch_launch_count.argtypes = [vp]
+    L.dilbm_batch_launch_count.restype = C.c_longlong
+    L.dilbm_batch_destroy.argtypes = [vp]
+    L.dilbm_batch_destroy.restype = None
     for name in ("dilbm_create", "dilbm_step", "dilbm_forces", "dilbm_fields", "dilbm_get_populations",
                  "dilbm_set_populations", "dilbm_set_particles", "dilbm_sync", "dilbm_set_timing",
-                 "dilbm_sweep_time"):
+                 "dilbm_sweep_time", "dilbm_batch_create", "dilbm_batch_step", "dilbm_batch_sync",
+                 "dilbm_batch_set_timing", "dilbm_batch_sweep_time"):
         getattr(L, name).restype = C.c_int
     if path == LIB_PATH:
         _lib = L
@@ -248,3 +258,50 @@ class Simulation:
     @property
     def launches(self) -> int:
         return int(self.L.dilbm_launch_count(self.h))
+
+
+class Batch:
+    """Several Simulations advanced together (``dilbm_batch_*``): one sweep and
+    one particle launch per step for all members, replayed from CUDA graphs.
+    The members stay usable on their own; they must outlive the batch."""
+
+    def __init__(self, sims):
+        self.L = load_library()
+        self.sims = list(sims)
+        arr = (C.c_void_p * len(self.sims))(*[s.h.value for s in self.sims])
+        h = C.c_void_p()
+        check(self.L.dilbm_batch_create(arr, len(self.sims), None, C.byref(h)))
+        self.h = h
+
+    def close(self) -> None:
+        if getattr(self, "h", None) is not None and self.h.value:
+            self.L.dilbm_batch_destroy(self.h)
+        self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def step(self, n: int = 1) -> None:
+        check(self.L.dilbm_batch_step(self.h, int(n)))
+
+    def sync(self) -> None:
+        bad = C.c_int(-1)
+        rc = self.L.dilbm_batch_sync(self.h, C.byref(bad))
+        if rc != OK:
+            raise DilbmError(rc, f"member {bad.value}: " + self.L.dilbm_last_error().decode(errors="replace"))
+
+    def set_timing(self, on: bool) -> None:
+        check(self.L.dilbm_batch_set_timing(self.h, 1 if on else 0))
+
+    def sweep_time(self):
+        ms = C.c_double()
+        n = C.c_longlong()
+        check(self.L.dilbm_batch_sweep_time(self.h, C.byref(ms), C.byref(n)))
+        return ms.value, n.value
+
+    @property
+    def launches(self) -> int:
+        return int(self.L.dilbm_batch_launch_count(self.h))
