@@ -43,13 +43,16 @@ def parse():
     ap.add_argument("--steps", type=int, default=4000)
     ap.add_argument("--warmup", type=int, default=20)
     ap.add_argument("--impl", default="dilbm", choices=["dilbm", "reference"])
-    ap.add_argument("--workload", default="periodic", choices=["periodic", "sedimentation", "cylinder", "batch"])
+    ap.add_argument("--workload", default="periodic", choices=["periodic", "sedimentation", "cylinder", "batch", "serve"])
     ap.add_argument("--storage", default="fp32", choices=["fp32", "fp16", "bf16"])
     ap.add_argument("--size", type=int, default=4096, help="periodic box edge")
     ap.add_argument("--particles", type=int, default=2048)
     ap.add_argument("--e2e-steps", type=int, default=200)
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--requests", type=int, default=300, help="serve: leading requests of the stream")
+    ap.add_argument("--max-jobs", type=int, default=64, help="serve: jobs resident at once")
+    ap.add_argument("--macro-steps", type=int, default=64, help="serve: steps per macro-step")
     return ap.parse_args()
 
 
@@ -427,12 +430,171 @@ def batch_arm(args):
     return 0
 
 
+def percentile(xs, q):
+    import numpy as np
+    return float(np.percentile(np.asarray(xs, dtype=float), q)) if len(xs) else None
+
+
+def replay_served(reqs, storage, args, D):
+    """Replay the arrival schedule in real time into a server; returns the
+    per-request latencies, results and the server's counters."""
+    srv = D.Server(storage, max_jobs=args.max_jobs, macro_steps=args.macro_steps)
+    t_base = srv.clock()
+    nxt = 0
+    ids = {}
+    while True:
+        now = srv.clock() - t_base
+        while nxt < len(reqs) and reqs[nxt].arrival_s <= now:
+            r = reqs[nxt]
+            ids[srv.submit(r.problem, r.steps, arrival=t_base + r.arrival_s, mean_window=r.steps // 4)] = nxt
+            nxt += 1
+        st = srv.progress()
+        if st.running == 0 and st.queued == 0:
+            if nxt == len(reqs):
+                break
+            time.sleep(max(0.0, reqs[nxt].arrival_s - (srv.clock() - t_base)))
+    lat, res, first, last = {}, {}, None, 0.0
+    for jid, k in ids.items():
+        js = srv.status(jid)
+        if js.state != D.JOB_DONE:
+            raise RuntimeError(f"request {k} ended in state {js.state} (error {js.error})")
+        lat[k] = js.finished - js.arrival
+        last = max(last, js.finished - t_base)
+        res[k] = srv.result(jid, with_mean=True)
+    first = reqs[0].arrival_s
+    srv_stats = st
+    srv.close()
+    return lat, res, last - first, srv_stats
+
+
+def replay_single(reqs, storage, D, stream):
+    """The plain single-instance path: one Simulation at a time in arrival
+    order (dilbm_create, dilbm_step(n), dilbm_forces), in real time."""
+    t_base = time.perf_counter()
+    lat, res, launches = {}, {}, 0
+    for k, r in enumerate(reqs):
+        now = time.perf_counter() - t_base
+        if now < r.arrival_s:
+            time.sleep(r.arrival_s - now)
+        sim = D.Simulation(r.problem, storage=storage, stream=stream)
+        sim.step(r.steps)
+        F, _, S = sim.forces()
+        launches += sim.launches
+        sim.close()
+        lat[k] = time.perf_counter() - t_base - r.arrival_s
+        res[k] = (F, None, S)
+    return lat, res, time.perf_counter() - t_base - reqs[0].arrival_s, launches
+
+
+def drag_errors(reqs, res_a, res_b):
+    """Per cylinder job: max over its discs of |Fx_a - Fx_b| / max |Fx_b|, on
+    the mean drag over the job's last quarter of steps."""
+    out = []
+    for k, r in enumerate(reqs):
+        if not r.problem.particles or not r.problem.particles[0].fixed:
+            continue
+        Fa, Fb = res_a[k][1], res_b[k][1]
+        scale = abs(Fb[:, 0]).max()
+        if scale > 0:
+            out.append(float(abs(Fa[:, 0] - Fb[:, 0]).max() / scale))
+    return out
+
+
+def serve_arm(args):
+    """The Poisson request stream (seed 5, 50 requests/s) served by continuous
+    batching in FP16 and FP32 deviation storage, against the plain
+    single-instance FP32 path on the same arrivals."""
+    import torch
+    from paper_2106_08950_gb300 import dilbm as D
+    from paper_2106_08950_gb300 import workloads as W
+
+    world, rank, local = dist_env()
+    torch.cuda.set_device(local)
+    dist = init_dist(world, "nccl")
+    dev = torch.device("cuda", local)
+    # replicas: rank k serves every world-th request of the stream
+    reqs = W.request_stream(count=args.requests * world)[rank::world]
+    work = sum(r.problem.nx * r.problem.ny * r.steps for r in reqs)
+    stream = torch.cuda.Stream(device=dev)
+    sh = int(stream.cuda_stream)
+    # warm-up: one small job through each path (module load, graph capture)
+    warm = [W.Request(0.0, 10, W.cylinder_drag())]
+    replay_served(warm, "fp16", args, D)
+    replay_single(warm, "fp32", D, sh)
+
+    arms = {}
+    clocks = ClockSampler(local)
+    clocks.start()
+    time.sleep(0.3)
+    barrier(dist)
+    for name, storage in (("served_fp16", "fp16"), ("served_fp32", "fp32")):
+        lat, res, span, st = replay_served(reqs, storage, args, D)
+        span = max_over_ranks(dist, span, dev)
+        arms[name] = {"lat": lat, "res": res, "span": span, "launches": st.launches,
+                      "host": {"macro_steps": st.macro_steps, "busy_s": st.busy_seconds, "form_s": st.form_seconds,
+                               "admit_s": st.admit_seconds, "wait_s": st.wait_seconds,
+                               "retire_s": st.retire_seconds}}
+        barrier(dist)
+    lat, res, span, launches = replay_single(reqs, "fp32", D, sh)
+    span = max_over_ranks(dist, span, dev)
+    arms["single_fp32"] = {"lat": lat, "res": res, "span": span, "launches": launches}
+    clk = clocks.stop()
+
+    def summary(a):
+        lv = list(a["lat"].values())
+        out = {"value": work * world / a["span"] / 1e6, "unit": "MLUPS", "p50_s": percentile(lv, 50),
+               "p99_s": percentile(lv, 99), "makespan_s": a["span"], "gpu_launches": a["launches"]}
+        if "host" in a:
+            out["server_time"] = a["host"]
+        return out
+
+    s16, s32, s1 = summary(arms["served_fp16"]), summary(arms["served_fp32"]), summary(arms["single_fp32"])
+    d16 = drag_errors(reqs, arms["served_fp16"]["res"], arms["served_fp32"]["res"])
+    parts_in = sum(len(r.problem.particles) for r in reqs)
+    import numpy as np
+    same = all(np.array_equal(arms["served_fp32"]["res"][k][0], arms["single_fp32"]["res"][k][0]) and
+               np.array_equal(arms["served_fp32"]["res"][k][2], arms["single_fp32"]["res"][k][2])
+               for k in range(len(reqs)))
+    line = {"metric": METRIC, "value": s16["value"], "unit": "MLUPS", "n_gpus": world, "steps": len(reqs),
+            "warmup": 1, "ms_per_step": None, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "f16-storage/f32-math", "data": "synthetic",
+            "config": {"workload": f"served: the first {len(reqs) * world} requests of a Poisson stream "
+                                   "(seed 5, 50 requests/s): cylinder or sedimentation jobs, nx, ny log-U[128,2048], "
+                                   "1-64 discs r U[5,15], steps log-U[1k,20k]; replayed in real time",
+                       "storage": "fp16", "node_updates": work * world, "max_jobs": args.max_jobs,
+                       "macro_steps": args.macro_steps, "admission": "FIFO by job slots and free device memory",
+                       "l2": "resident lattices exceed L2 once a few large jobs run; no flush",
+                       "parallelism": f"replicas x{world}" if world > 1 else "single GPU"},
+            "latency": {"p50_s": s16["p50_s"], "p99_s": s16["p99_s"]},
+            "server_time": s16.get("server_time"),
+            "served_fp32": s32, "single_instance_fp32": s1,
+            "gain_over_single_fp32": {"mlups": s16["value"] / s1["value"], "p50": s1["p50_s"] / s16["p50_s"],
+                                      "p99": s1["p99_s"] / s16["p99_s"]},
+            "drag_error_fp16_vs_fp32": {"jobs": len(d16), "median": percentile(d16, 50), "p90": percentile(d16, 90),
+                                        "p99": percentile(d16, 99), "max": max(d16) if d16 else None,
+                                        "quantity": "mean F_x over each cylinder job's last quarter of steps"},
+            "fp32_served_equals_single_bitwise": same,
+            "roofline": None, "gpu_launches": s16["gpu_launches"],
+            "e2e": {"value": s16["value"], "unit": "MLUPS", "h2d_bytes_per_step": None, "d2h_bytes_per_step": None,
+                    "h2d_bytes_per_request": parts_in * 72 // max(1, len(reqs)),
+                    "d2h_bytes_per_request": parts_in * (72 + 24) // max(1, len(reqs)),
+                    "note": "the served value is end to end: host job descriptions in, host results out"},
+            "clocks": clk}
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if dist is not None:
+        dist.destroy_process_group()
+    return 0
+
+
 def main():
     args = parse()
     if args.impl == "reference":
         return reference_arm(args)
     if args.workload == "batch":
         return batch_arm(args)
+    if args.workload == "serve":
+        return serve_arm(args)
     return gpu_arm(args)
 
 

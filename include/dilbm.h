@@ -129,6 +129,16 @@ int dilbm_step(dilbm_ctx *ctx, long long nsteps);
 int dilbm_forces(dilbm_ctx *ctx, double *force, double *fcol, dilbm_particle *state);
 
 /*
+ * Time mean of the hydrodynamic force and torque (Eqs. 18-19) over the steps
+ * since create or the last dilbm_force_mean_reset(): mean host np x 3
+ * (Fx, Fy, T); *nsteps receives the number of steps averaged (the mean is 0
+ * when it is 0).  Each step adds its force in FP64 on the device.
+ * dilbm_force_mean synchronises the stream; the reset is asynchronous.
+ */
+int dilbm_force_mean(dilbm_ctx *ctx, double *mean, long long *nsteps);
+int dilbm_force_mean_reset(dilbm_ctx *ctx);
+
+/*
  * Macroscopic fields at the current time level, row-major [ny][nx] FP32:
  * density (Eq. 5), corrected velocity (Eq. 17) and solid fraction (Eq. 14),
  * taken from the populations the next step would collide.  Any pointer may be
@@ -182,7 +192,10 @@ long long dilbm_launch_count(const dilbm_ctx *ctx);
  *   dilbm_step) may be mixed with batch steps.  cuda_stream is unused.
  * dilbm_batch_step: advance every member nsteps (asynchronous).
  * dilbm_batch_sync: wait; return the first member's sticky device error and
- *   its index in *first_failed (-1 if none; pointer may be NULL).
+ *   its index in *first_failed (-1 if none; pointer may be NULL).  Every
+ *   member's error word is read with one copy.
+ * dilbm_batch_errors: wait; codes[k] (host, n ints) receives member k's error
+ *   (DILBM_OK, UNSTABLE, TIMEOUT or OVERFLOW).  Returns CUDA on a CUDA error.
  * dilbm_batch_set_timing / dilbm_batch_sweep_time: CUDA events around every
  *   batched sweep launch (timing replaces graph replay by direct launches).
  * dilbm_batch_launch_count: kernels the batch has launched.
@@ -191,10 +204,117 @@ typedef struct dilbm_batch dilbm_batch;
 int dilbm_batch_create(dilbm_ctx *const *members, int n, void *cuda_stream, dilbm_batch **out);
 int dilbm_batch_step(dilbm_batch *batch, long long nsteps);
 int dilbm_batch_sync(dilbm_batch *batch, int *first_failed);
+int dilbm_batch_errors(dilbm_batch *batch, int *codes);
 int dilbm_batch_set_timing(dilbm_batch *batch, int enable);
 int dilbm_batch_sweep_time(dilbm_batch *batch, double *ms_total, long long *launches);
 long long dilbm_batch_launch_count(const dilbm_batch *batch);
 void dilbm_batch_destroy(dilbm_batch *batch);
+
+/*
+ * Device memory dilbm_create allocates for a lattice of grid->nx x grid->ny
+ * with np particles in grid->storage (populations A and B, tile bins, force
+ * partials, particle state).  The driver rounds each allocation up, so the
+ * memory actually taken is slightly larger.  Host-only arithmetic.
+ * Errors: INVALID_ARG (NULL pointer, bad size or storage).
+ */
+int dilbm_footprint(const dilbm_grid *grid, int np, unsigned long long *bytes);
+
+/*
+ * Serving: a request loop that keeps every admitted lattice resident on the
+ * device and advances all of them together (continuous batching).  The
+ * method is unchanged: each job is the DI-LBM problem of dilbm_create,
+ * advanced nsteps steps (Eqs. 13-19, 22-24, 28-29), and its result is bit for
+ * bit the one dilbm_step gives it alone.
+ *
+ * A job is queued at submit (host only).  dilbm_server_progress() runs one
+ * macro-step: it launches the next k steps of every running job as one batch
+ * (k = min(macro_steps, fewest steps any running job has left, steps until
+ * any job's mean-force window opens)), admits
+ * queued jobs while the GPU works -- in arrival order, while a job slot is
+ * free and the job's dilbm_footprint fits the memory budget -- then waits for
+ * the k steps, retires the jobs that reached their step count (their forces
+ * and particle state are copied to the host and their device memory freed)
+ * and re-forms the batch from the running jobs.  Jobs admitted in one call
+ * start their steps in the next.
+ *
+ * Times are seconds on the server's clock (a monotonic host clock, zero at
+ * create; dilbm_server_clock()).  One host thread drives a server.
+ */
+typedef enum {
+    DILBM_ADMIT_FIFO = 0,       /* admit in arrival order; stop at the first job that does not fit */
+    DILBM_ADMIT_FIRST_FIT = 1   /* admit every queued job that fits, in arrival order */
+} dilbm_admit_policy;
+
+typedef struct {
+    int storage;                /* dilbm_storage of every job (a job's grid.storage is ignored) */
+    int max_jobs;               /* jobs resident at once, 1..1024 */
+    long long macro_steps;      /* most steps per macro-step, >= 1 */
+    double memory_budget;       /* bytes the resident jobs may take; <= 0: 90% of free device memory at create */
+    int policy;                 /* dilbm_admit_policy */
+} dilbm_server_config;
+
+typedef struct {
+    dilbm_grid grid;            /* as for dilbm_create */
+    double tau, interface_width;
+    const dilbm_particle *particles;   /* host, np entries, copied at submit */
+    int np;
+    long long nsteps;           /* >= 1 */
+    long long mean_window;      /* 0..nsteps: the result also carries the time mean of the force
+                                   over the job's last mean_window steps (dilbm_force_mean) */
+    double arrival;             /* server-clock time the request arrived; < 0: the submit time */
+} dilbm_job;
+
+typedef enum {
+    DILBM_JOB_QUEUED = 0,
+    DILBM_JOB_RUNNING = 1,
+    DILBM_JOB_DONE = 2,
+    DILBM_JOB_FAILED = 3
+} dilbm_job_state;
+
+typedef struct {
+    int state;                  /* dilbm_job_state */
+    int error;                  /* DILBM_OK, or the code that failed the job */
+    int np;
+    long long steps_done;
+    double arrival, admitted, finished;   /* server clock; -1 until reached */
+    unsigned long long footprint;         /* dilbm_footprint of the job */
+} dilbm_job_status;
+
+typedef struct {
+    int running, queued;
+    long long done, failed;
+    long long macro_steps;      /* macro-steps run so far */
+    double node_updates;        /* sum over finished steps of the running jobs' nodes */
+    double busy_seconds;        /* host time spent inside dilbm_server_progress, of which: */
+    double form_seconds;        /*   forming batches and launching macro-steps */
+    double admit_seconds;       /*   setting up admitted jobs (mostly while the GPU steps) */
+    double wait_seconds;        /*   waiting for macro-steps to finish */
+    double retire_seconds;      /*   reading results and freeing finished jobs (the GPU is idle) */
+    unsigned long long memory_in_use;     /* sum of the running jobs' footprints */
+    long long launches;         /* kernels launched for the jobs so far */
+} dilbm_server_stats;
+
+typedef struct dilbm_server dilbm_server;
+
+/* Create a server; cuda_stream (NULL: a private stream) carries the jobs'
+ * set-up and read-back.  Errors: INVALID_ARG, CUDA. */
+int dilbm_server_create(const dilbm_server_config *cfg, void *cuda_stream, dilbm_server **out);
+/* Queue a job; *id receives its handle (>= 0).  A job whose footprint exceeds
+ * the budget is rejected here with INVALID_ARG. */
+int dilbm_server_submit(dilbm_server *srv, const dilbm_job *job, long long *id);
+/* One macro-step (see above); *stats (nullable) receives the counters after it. */
+int dilbm_server_progress(dilbm_server *srv, dilbm_server_stats *stats);
+/* State and timestamps of a job. */
+int dilbm_server_status(const dilbm_server *srv, long long id, dilbm_job_status *st);
+/* Result of a DONE job: force (host, np x 3: Fx, Fy, T of its last step,
+ * Eqs. 18-19), force_mean (host, np x 3, nullable: their mean over the job's
+ * last mean_window steps) and state (host, np entries, nullable); then its
+ * record is released.  Errors: INVALID_ARG (unknown id or job not DONE). */
+int dilbm_server_result(dilbm_server *srv, long long id, double *force, double *force_mean,
+                        dilbm_particle *state);
+double dilbm_server_clock(const dilbm_server *srv);
+/* Free every job and the server (synchronises). */
+void dilbm_server_destroy(dilbm_server *srv);
 
 /*
  * One time step that allocates no device memory.  The paper has no

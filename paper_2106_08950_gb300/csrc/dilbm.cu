@@ -46,6 +46,8 @@ struct dilbm_ctx {
     Bins bins[2]{};                   // tile bins by step parity
     float4 *partial = nullptr;        // per tile, slot and row: force / torque partials
     double *force = nullptr, *fcol = nullptr;
+    double *fsum = nullptr;           // per particle: sum of (Fx, Fy, T) since the last reset
+    long long fsum_steps = 0;
     int *err = nullptr;
     int sticky = 0;
     float *fields = nullptr;          // 4 x nx x ny, allocated on first use
@@ -106,10 +108,27 @@ void set_wrap_flags(dilbm_ctx *c, const dilbm_particle *p, int np) {
     c->L.wrap_y = c->L.per_y && c->L.ny < reach + TILE_H;
 }
 
-int check_reach(dilbm_ctx *c, const dilbm_particle *p, int np) {
+// Bytes of the device allocations dilbm_create makes (kept beside it: the
+// same arrays, in the same order).
+unsigned long long footprint_of(int nx, int ny, size_t elem, int np) {
+    const unsigned long long pitch = (unsigned long long)(nx + 31) / 32 * 32;
+    const unsigned long long plane = pitch * (unsigned long long)ny;
+    const unsigned long long ntiles =
+        (unsigned long long)((nx + TILE_W - 1) / TILE_W) * (unsigned long long)((ny + TILE_H - 1) / TILE_H);
+    const unsigned long long npa = np > 0 ? (unsigned long long)np : 1ull;
+    unsigned long long b = 2ull * (9ull * plane + 2ull * GUARD) * elem;           // populations A, B
+    b += 10ull * npa * sizeof(double) + 4ull * npa * sizeof(float) + npa * sizeof(int);   // particle state
+    b += 6ull * npa * sizeof(double) + 2ull * npa * sizeof(double) + sizeof(int);         // force, fsum, fcol, err
+    b += ntiles * MAXC * TILE_H * sizeof(float4);                                         // partials
+    b += 2ull * (ntiles * sizeof(int) + ntiles * MAXC * sizeof(int) + ntiles * MAXC * NREC * sizeof(float4) +
+                 npa * MAXT * sizeof(int) + npa * sizeof(int));                           // bins, two parities
+    return b;
+}
+
+int check_reach(double cut_d, const dilbm_particle *p, int np) {
     // tiles one particle's phi tail may reach must fit the per-particle map
     for (int k = 0; k < np; ++k) {
-        const double R = p[k].r + c->ph.cut_d;
+        const double R = p[k].r + cut_d;
         const long long tx = (long long)std::ceil((2.0 * R + 2.0) / TILE_W) + 1;
         const long long ty = (long long)std::ceil((2.0 * R + 2.0) / TILE_H) + 1;
         if (tx * ty > MAXT)
@@ -135,6 +154,7 @@ PartArgs particle_args(const dilbm_ctx *c, int cur, int integrate) {
     a.integrate = integrate;
     a.force = c->force;
     a.fcol = c->fcol;
+    a.fsum = integrate ? c->fsum : nullptr;
     a.err = c->err;
     return a;
 }
@@ -150,7 +170,7 @@ int launch_particles(dilbm_ctx *c, int integrate) {
 
 int upload_particles(dilbm_ctx *c, const dilbm_particle *p, int np) {
     set_wrap_flags(c, p, np);
-    int rc = check_reach(c, p, np);
+    int rc = check_reach(c->ph.cut_d, p, np);
     if (rc) return rc;
     std::vector<double> h(8 * (size_t)np);
     std::vector<int> fx(np);
@@ -266,7 +286,27 @@ int one_step(dilbm_ctx *c) {
     if (c->timing) DILBM_CUDA(cudaEventRecord(e1, c->stream));
     if (c->np > 0 && (rc = launch_particles(c, 1))) return rc;
     c->cur ^= 1;
+    c->fsum_steps += 1;
     return DILBM_OK;
+}
+
+// The C ABI code of a lattice's sticky error bits (the first in the order
+// UNSTABLE, TIMEOUT, OVERFLOW), and that code with its message.
+int sticky_code(int bits) {
+    if (bits & ERR_UNSTABLE) return DILBM_ERR_UNSTABLE;
+    if (bits & ERR_TIMEOUT) return DILBM_ERR_TIMEOUT;
+    if (bits & ERR_OVERFLOW) return DILBM_ERR_OVERFLOW;
+    return DILBM_OK;
+}
+
+int sticky_error(int bits) {
+    switch (sticky_code(bits)) {
+    case DILBM_ERR_UNSTABLE: return fail(DILBM_ERR_UNSTABLE, "a node reached rho <= 0 or a non-finite velocity");
+    case DILBM_ERR_TIMEOUT: return fail(DILBM_ERR_TIMEOUT, "a bounded device wait gave up (1 s)");
+    case DILBM_ERR_OVERFLOW:
+        return fail(DILBM_ERR_OVERFLOW, "more than DILBM_MAX_CANDIDATES particles reach one lattice tile");
+    default: return DILBM_OK;
+    }
 }
 
 int read_sticky(dilbm_ctx *c) {
@@ -274,11 +314,7 @@ int read_sticky(dilbm_ctx *c) {
     DILBM_CUDA(cudaMemcpyAsync(&h, c->err, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
     DILBM_CUDA(cudaStreamSynchronize(c->stream));
     c->sticky |= h;
-    if (c->sticky & ERR_UNSTABLE) return fail(DILBM_ERR_UNSTABLE, "a node reached rho <= 0 or a non-finite velocity");
-    if (c->sticky & ERR_TIMEOUT) return fail(DILBM_ERR_TIMEOUT, "a bounded device wait gave up (1 s)");
-    if (c->sticky & ERR_OVERFLOW)
-        return fail(DILBM_ERR_OVERFLOW, "more than DILBM_MAX_CANDIDATES particles reach one lattice tile");
-    return DILBM_OK;
+    return sticky_error(c->sticky);
 }
 
 }  // namespace
@@ -286,16 +322,10 @@ int read_sticky(dilbm_ctx *c) {
 namespace dilbm {
 // Lets other translation units of the library report through dilbm_last_error().
 int set_last_error(int code, const std::string &msg) { return fail(code, msg); }
-}  // namespace dilbm
 
-extern "C" {
-
-const char *dilbm_last_error(void) { return g_err.c_str(); }
-
-int dilbm_create(const dilbm_grid *g, dilbm_lattice lattice, double tau, double interface_width,
-                 const dilbm_particle *particles, int np, void *cuda_stream, dilbm_ctx **out) {
-    if (!g || !out) return fail(DILBM_ERR_INVALID_ARG, "grid and out must not be NULL");
-    *out = nullptr;
+// Every argument check of dilbm_create (host only; g must not be NULL).
+int check_problem(const dilbm_grid *g, dilbm_lattice lattice, double tau, double interface_width,
+                  const dilbm_particle *particles, int np) {
     if (lattice != DILBM_D2Q9) return fail(DILBM_ERR_INVALID_ARG, "only DILBM_D2Q9 is supported");
     if (g->nx < 3 || g->ny < 3) return fail(DILBM_ERR_INVALID_ARG, "nx and ny must be >= 3");
     if ((long long)g->nx * g->ny > (1LL << 31)) return fail(DILBM_ERR_INVALID_ARG, "lattice larger than 2^31 nodes");
@@ -316,6 +346,20 @@ int dilbm_create(const dilbm_grid *g, dilbm_lattice lattice, double tau, double 
     for (int k = 0; k < 5; ++k)
         if (!(g->wan_turek[k] > 0.0)) return fail(DILBM_ERR_INVALID_ARG, "Wan-Turek parameters must be > 0");
     if ((rc = check_particles(g, particles, np))) return rc;
+    return check_reach(PHI_CUT_WIDTHS * interface_width, particles, np);
+}
+}  // namespace dilbm
+
+extern "C" {
+
+const char *dilbm_last_error(void) { return g_err.c_str(); }
+
+int dilbm_create(const dilbm_grid *g, dilbm_lattice lattice, double tau, double interface_width,
+                 const dilbm_particle *particles, int np, void *cuda_stream, dilbm_ctx **out) {
+    if (!g || !out) return fail(DILBM_ERR_INVALID_ARG, "grid and out must not be NULL");
+    *out = nullptr;
+    int rc = dilbm::check_problem(g, lattice, tau, interface_width, particles, np);
+    if (rc) return rc;
 
     dilbm_ctx *c = new dilbm_ctx();
     c->stream = (cudaStream_t)cuda_stream;
@@ -381,7 +425,8 @@ int dilbm_create(const dilbm_grid *g, dilbm_lattice lattice, double tau, double 
     float *pf = nullptr;
     if ((rc = dev_alloc(c, &pd, 10 * (size_t)npa)) || (rc = dev_alloc(c, &pf, 4 * (size_t)npa)) ||
         (rc = dev_alloc(c, &c->P.fixed, (size_t)npa)) || (rc = dev_alloc(c, &c->force, 3 * (size_t)npa)) ||
-        (rc = dev_alloc(c, &c->fcol, 2 * (size_t)npa)) || (rc = dev_alloc(c, &c->err, 1)) ||
+        (rc = dev_alloc(c, &c->fsum, 3 * (size_t)npa)) || (rc = dev_alloc(c, &c->fcol, 2 * (size_t)npa)) ||
+        (rc = dev_alloc(c, &c->err, 1)) ||
         (rc = dev_alloc(c, &c->partial, (size_t)c->ntiles * MAXC * TILE_H)))
         return bail(rc);
     for (int b = 0; b < 2; ++b) {
@@ -398,6 +443,7 @@ int dilbm_create(const dilbm_grid *g, dilbm_lattice lattice, double tau, double 
     cudaError_t e;
     if ((e = cudaMemsetAsync(c->err, 0, sizeof(int), c->stream)) != cudaSuccess ||
         (e = cudaMemsetAsync(c->force, 0, sizeof(double) * 3 * npa, c->stream)) != cudaSuccess ||
+        (e = cudaMemsetAsync(c->fsum, 0, sizeof(double) * 3 * npa, c->stream)) != cudaSuccess ||
         (e = cudaMemsetAsync(c->fcol, 0, sizeof(double) * 2 * npa, c->stream)) != cudaSuccess ||
         (e = cudaMemsetAsync(c->bins[0].count, 0, sizeof(int) * c->ntiles, c->stream)) != cudaSuccess ||
         (e = cudaMemsetAsync(c->bins[1].count, 0, sizeof(int) * c->ntiles, c->stream)) != cudaSuccess)
@@ -456,6 +502,25 @@ int dilbm_forces(dilbm_ctx *c, double *force, double *fcol, dilbm_particle *stat
         }
     }
     return rc;
+}
+
+int dilbm_force_mean(dilbm_ctx *c, double *mean, long long *nsteps) {
+    if (!c || !nsteps || (c->np > 0 && !mean)) return fail(DILBM_ERR_INVALID_ARG, "NULL argument");
+    const int np = c->np;
+    *nsteps = c->fsum_steps;
+    if (np == 0) return read_sticky(c);
+    DILBM_CUDA(cudaMemcpyAsync(mean, c->fsum, sizeof(double) * 3 * np, cudaMemcpyDeviceToHost, c->stream));
+    const int rc = read_sticky(c);   // synchronises the stream
+    const double inv = c->fsum_steps > 0 ? 1.0 / (double)c->fsum_steps : 0.0;
+    for (int k = 0; k < 3 * np; ++k) mean[k] *= inv;
+    return rc;
+}
+
+int dilbm_force_mean_reset(dilbm_ctx *c) {
+    if (!c) return fail(DILBM_ERR_INVALID_ARG, "NULL context");
+    if (c->np > 0) DILBM_CUDA(cudaMemsetAsync(c->fsum, 0, sizeof(double) * 3 * c->np, c->stream));
+    c->fsum_steps = 0;
+    return DILBM_OK;
 }
 
 int dilbm_fields(dilbm_ctx *c, float *rho, float *ux, float *uy, float *phi, int on_device) {
@@ -569,6 +634,13 @@ int dilbm_sweep_time(dilbm_ctx *c, double *ms_total, long long *launches) {
 
 long long dilbm_launch_count(const dilbm_ctx *c) { return c ? c->launches : -1; }
 
+int dilbm_footprint(const dilbm_grid *g, int np, unsigned long long *bytes) {
+    if (!g || !bytes || np < 0 || g->nx < 3 || g->ny < 3 || g->storage < DILBM_FP32 || g->storage > DILBM_BF16_DEV)
+        return fail(DILBM_ERR_INVALID_ARG, "dilbm_footprint: bad grid, particle count or output pointer");
+    *bytes = footprint_of(g->nx, g->ny, g->storage == DILBM_FP32 ? 4 : 2, np);
+    return DILBM_OK;
+}
+
 }  // extern "C"
 
 // ---------------------------------------------------------------- batches
@@ -586,6 +658,9 @@ struct dilbm_batch {
     std::vector<void *> sweep_params[2];   // BatchArgs<T> per launch group, per phase (host copies)
     PartArgs *part_args[2] = {nullptr, nullptr};
     int *part_start = nullptr;          // n + 1
+    int *const *err_ptrs = nullptr;     // device: every member's error word
+    int *err_out = nullptr;             // device: their values, gathered for one copy
+    std::vector<int> err_host;
     int nparts = 0;
     std::vector<int> group_blocks;      // persistent grid of each launch group
     cudaGraphExec_t g_pair = nullptr, g_single[2] = {nullptr, nullptr};
@@ -598,6 +673,12 @@ struct dilbm_batch {
 namespace {
 
 constexpr int MAX_BATCH = 1024;
+
+// Copies every member's error word into one array, so that a batch sync
+// reads them all with a single device-to-host copy.
+__global__ void gather_errors_kernel(int *const *__restrict__ err, int n, int *__restrict__ out) {
+    for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < n; k += gridDim.x * blockDim.x) out[k] = *err[k];
+}
 
 void free_sweep_params(dilbm_batch *b) {
     for (int phase = 0; phase < 2; ++phase) {
@@ -785,6 +866,17 @@ int dilbm_batch_create(dilbm_ctx *const *members, int n, void *cuda_stream, dilb
     if ((e = cudaMalloc((void **)&b->part_start, sizeof(int) * (n + 1))) != cudaSuccess ||
         (e = cudaMemcpy(b->part_start, ps.data(), sizeof(int) * (n + 1), cudaMemcpyHostToDevice)) != cudaSuccess)
         return bail(cuda_fail(e, "batch particle list"));
+    {
+        std::vector<int *> ep(n);
+        for (int k = 0; k < n; ++k) ep[k] = members[k]->err;
+        void *q = nullptr;
+        if ((e = cudaMalloc(&q, sizeof(int *) * n)) != cudaSuccess) return bail(cuda_fail(e, "cudaMalloc batch errors"));
+        b->err_ptrs = static_cast<int *const *>(q);
+        if ((e = cudaMemcpy(q, ep.data(), sizeof(int *) * n, cudaMemcpyHostToDevice)) != cudaSuccess ||
+            (e = cudaMalloc((void **)&b->err_out, sizeof(int) * n)) != cudaSuccess)
+            return bail(cuda_fail(e, "batch error words"));
+        b->err_host.assign(n, 0);
+    }
     // order after every member's queued work, then build the launches
     for (cudaStream_t s : b->member_streams) {
         if ((e = cudaEventRecord(b->ev_in, s)) != cudaSuccess || (e = cudaStreamWaitEvent(b->stream, b->ev_in, 0)) != cudaSuccess)
@@ -830,6 +922,7 @@ int dilbm_batch_step(dilbm_batch *b, long long nsteps) {
     for (size_t k = 0; k < b->members.size(); ++k) {
         dilbm_ctx *c = b->members[k];
         c->cur = b->cur0[k] ^ (int)(b->done & 1);
+        c->fsum_steps += nsteps;
     }
     // members' own streams see the batch's work before anything queued later
     DILBM_CUDA(cudaEventRecord(b->ev_out, b->stream));
@@ -839,15 +932,30 @@ int dilbm_batch_step(dilbm_batch *b, long long nsteps) {
 
 int dilbm_batch_sync(dilbm_batch *b, int *first_failed) {
     if (!b) return fail(DILBM_ERR_INVALID_ARG, "NULL batch");
+    const int n = (int)b->members.size();
+    gather_errors_kernel<<<(n + 255) / 256, 256, 0, b->stream>>>(b->err_ptrs, n, b->err_out);
+    DILBM_CUDA(cudaGetLastError());
+    b->launches += 1;
+    DILBM_CUDA(cudaMemcpyAsync(b->err_host.data(), b->err_out, sizeof(int) * n, cudaMemcpyDeviceToHost, b->stream));
     DILBM_CUDA(cudaStreamSynchronize(b->stream));
     if (first_failed) *first_failed = -1;
-    for (size_t k = 0; k < b->members.size(); ++k) {
-        int rc = read_sticky(b->members[k]);
-        if (rc) {
-            if (first_failed) *first_failed = (int)k;
-            return rc;
+    for (int k = 0; k < n; ++k) {
+        dilbm_ctx *c = b->members[k];
+        c->sticky |= b->err_host[k];
+        if (c->sticky) {
+            if (first_failed) *first_failed = k;
+            return sticky_error(c->sticky);
         }
     }
+    return DILBM_OK;
+}
+
+int dilbm_batch_errors(dilbm_batch *b, int *codes) {
+    if (!b || !codes) return fail(DILBM_ERR_INVALID_ARG, "NULL argument");
+    int first = -1;
+    int rc = dilbm_batch_sync(b, &first);
+    if (rc != DILBM_OK && first < 0) return rc;      // a CUDA error, not a member's
+    for (size_t k = 0; k < b->members.size(); ++k) codes[k] = sticky_code(b->members[k]->sticky);
     return DILBM_OK;
 }
 
@@ -885,6 +993,8 @@ void dilbm_batch_destroy(dilbm_batch *b) {
     }
     free_sweep_params(b);
     cudaFree(b->part_start);
+    cudaFree((void *)b->err_ptrs);
+    cudaFree(b->err_out);
     for (cudaEvent_t e : b->ev) cudaEventDestroy(e);
     if (b->ev_in) cudaEventDestroy(b->ev_in);
     if (b->ev_out) cudaEventDestroy(b->ev_out);

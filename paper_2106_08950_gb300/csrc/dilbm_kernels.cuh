@@ -1030,6 +1030,7 @@ struct PartArgs {
     int pin, pout;              // position copy read / written
     int integrate;
     double *force, *fcol;
+    double *fsum;               // nullable: running sum of (Fx, Fy, T) over integrating steps
     int *err;
 };
 
@@ -1161,6 +1162,9 @@ __device__ __forceinline__ void particle_body(const PartArgs &A, int p, int lane
         if (lane == 0) {
             force[3 * p] = fx; force[3 * p + 1] = fy; force[3 * p + 2] = tq;
             fcol[2 * p] = cx; fcol[2 * p + 1] = cy;
+            if (A.fsum) {
+                A.fsum[3 * p] += fx; A.fsum[3 * p + 1] += fy; A.fsum[3 * p + 2] += tq;
+            }
             if (!P.fixed[p]) {
                 P.ux[p] = ux; P.uy[p] = uy; P.omega[p] = om;
                 P.theta[p] += om;

@@ -55,6 +55,33 @@ class Particle(C.Structure):
                 ("theta", C.c_double), ("rho_s", C.c_double), ("fixed", C.c_int)]
 
 
+class ServerConfig(C.Structure):
+    _fields_ = [("storage", C.c_int), ("max_jobs", C.c_int), ("macro_steps", C.c_longlong),
+                ("memory_budget", C.c_double), ("policy", C.c_int)]
+
+
+class Job(C.Structure):
+    _fields_ = [("grid", Grid), ("tau", C.c_double), ("interface_width", C.c_double),
+                ("particles", C.POINTER(Particle)), ("np", C.c_int), ("nsteps", C.c_longlong),
+                ("mean_window", C.c_longlong), ("arrival", C.c_double)]
+
+
+class JobStatus(C.Structure):
+    _fields_ = [("state", C.c_int), ("error", C.c_int), ("np", C.c_int), ("steps_done", C.c_longlong),
+                ("arrival", C.c_double), ("admitted", C.c_double), ("finished", C.c_double),
+                ("footprint", C.c_ulonglong)]
+
+
+class ServerStats(C.Structure):
+    _fields_ = [("running", C.c_int), ("queued", C.c_int), ("done", C.c_longlong), ("failed", C.c_longlong),
+                ("macro_steps", C.c_longlong), ("node_updates", C.c_double), ("busy_seconds", C.c_double),
+                ("form_seconds", C.c_double), ("admit_seconds", C.c_double), ("wait_seconds", C.c_double),
+                ("retire_seconds", C.c_double), ("memory_in_use", C.c_ulonglong), ("launches", C.c_longlong)]
+
+
+JOB_QUEUED, JOB_RUNNING, JOB_DONE, JOB_FAILED = 0, 1, 2, 3
+ADMIT_FIFO, ADMIT_FIRST_FIT = 0, 1
+
 _lib = None
 
 
@@ -98,10 +125,25 @@ def load_library(path: Optional[str] = None):
     L.dilbm_batch_launch_count.restype = C.c_longlong
     L.dilbm_batch_destroy.argtypes = [vp]
     L.dilbm_batch_destroy.restype = None
+    L.dilbm_batch_errors.argtypes = [vp, C.POINTER(C.c_int)]
+    L.dilbm_footprint.argtypes = [C.POINTER(Grid), ip, C.POINTER(C.c_ulonglong)]
+    L.dilbm_server_create.argtypes = [C.POINTER(ServerConfig), vp, C.POINTER(vp)]
+    L.dilbm_server_submit.argtypes = [vp, C.POINTER(Job), C.POINTER(C.c_longlong)]
+    L.dilbm_server_progress.argtypes = [vp, C.POINTER(ServerStats)]
+    L.dilbm_server_status.argtypes = [vp, C.c_longlong, C.POINTER(JobStatus)]
+    L.dilbm_server_result.argtypes = [vp, C.c_longlong, vp, vp, vp]
+    L.dilbm_force_mean.argtypes = [vp, vp, C.POINTER(C.c_longlong)]
+    L.dilbm_force_mean_reset.argtypes = [vp]
+    L.dilbm_server_clock.argtypes = [vp]
+    L.dilbm_server_clock.restype = C.c_double
+    L.dilbm_server_destroy.argtypes = [vp]
+    L.dilbm_server_destroy.restype = None
     for name in ("dilbm_create", "dilbm_step", "dilbm_forces", "dilbm_fields", "dilbm_get_populations",
                  "dilbm_set_populations", "dilbm_set_particles", "dilbm_sync", "dilbm_set_timing",
                  "dilbm_sweep_time", "dilbm_batch_create", "dilbm_batch_step", "dilbm_batch_sync",
-                 "dilbm_batch_set_timing", "dilbm_batch_sweep_time"):
+                 "dilbm_batch_set_timing", "dilbm_batch_sweep_time", "dilbm_batch_errors", "dilbm_footprint",
+                 "dilbm_server_create", "dilbm_server_submit", "dilbm_server_progress", "dilbm_server_status",
+                 "dilbm_server_result", "dilbm_force_mean", "dilbm_force_mean_reset"):
         getattr(L, name).restype = C.c_int
     if path == LIB_PATH:
         _lib = L
@@ -146,6 +188,14 @@ def particles_to_array(arr, n) -> np.ndarray:
         q = arr[k]
         out[k] = (q.x, q.y, q.r, q.ux, q.uy, q.omega, q.theta, q.rho_s)
     return out
+
+
+def footprint(prob: W.Problem, storage: str = "fp32") -> int:
+    """Device bytes ``dilbm_create`` allocates for ``prob`` (host arithmetic)."""
+    g = make_grid(prob, storage)
+    out = C.c_ulonglong()
+    check(load_library().dilbm_footprint(C.byref(g), len(prob.particles), C.byref(out)))
+    return int(out.value)
 
 
 def current_stream_handle() -> int:
@@ -209,6 +259,17 @@ class Simulation:
         st = (Particle * n)()
         check(self.L.dilbm_forces(self.h, F.ctypes.data, Fc.ctypes.data, C.cast(st, C.c_void_p)))
         return F[: self.np], Fc[: self.np], particles_to_array(st, self.np)
+
+    def force_mean(self):
+        """(np, 3) mean Fx, Fy, T since create or the last reset, and the steps averaged."""
+        n = max(1, self.np)
+        M = np.zeros((n, 3))
+        k = C.c_longlong()
+        check(self.L.dilbm_force_mean(self.h, M.ctypes.data, C.byref(k)))
+        return M[: self.np], int(k.value)
+
+    def force_mean_reset(self) -> None:
+        check(self.L.dilbm_force_mean_reset(self.h))
 
     def forces_into(self, F: np.ndarray) -> None:
         """Copy Fx, Fy, T of the last step into a host array of np x 3 doubles."""
@@ -305,3 +366,66 @@ class Batch:
     @property
     def launches(self) -> int:
         return int(self.L.dilbm_batch_launch_count(self.h))
+
+
+class Server:
+    """Continuous batching of DI-LBM jobs (``dilbm_server_*``): jobs are
+    admitted by free slots and a device memory budget and every running job
+    advances in one batch per macro-step."""
+
+    def __init__(self, storage: str = "fp32", max_jobs: int = 256, macro_steps: int = 64,
+                 memory_budget: float = 0.0, policy: int = ADMIT_FIFO):
+        self.L = load_library()
+        self.storage = storage
+        cfg = ServerConfig(STORAGE[storage], int(max_jobs), int(macro_steps), float(memory_budget), int(policy))
+        h = C.c_void_p()
+        check(self.L.dilbm_server_create(C.byref(cfg), None, C.byref(h)))
+        self.h = h
+        self.np = {}
+
+    def close(self) -> None:
+        if getattr(self, "h", None) is not None and self.h.value:
+            self.L.dilbm_server_destroy(self.h)
+        self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def clock(self) -> float:
+        return float(self.L.dilbm_server_clock(self.h))
+
+    def submit(self, prob: W.Problem, nsteps: int, arrival: float = -1.0, mean_window: int = 0) -> int:
+        parts = make_particles(prob.particles)
+        job = Job(make_grid(prob, self.storage), prob.tau, prob.eps, C.cast(parts, C.POINTER(Particle)),
+                  len(prob.particles), int(nsteps), int(mean_window), float(arrival))
+        jid = C.c_longlong()
+        check(self.L.dilbm_server_submit(self.h, C.byref(job), C.byref(jid)))
+        self.np[jid.value] = len(prob.particles)
+        return int(jid.value)
+
+    def progress(self) -> ServerStats:
+        st = ServerStats()
+        check(self.L.dilbm_server_progress(self.h, C.byref(st)))
+        return st
+
+    def status(self, jid: int) -> JobStatus:
+        st = JobStatus()
+        check(self.L.dilbm_server_status(self.h, int(jid), C.byref(st)))
+        return st
+
+    def result(self, jid: int, with_mean: bool = False):
+        """(np, 3) Fx, Fy, T of the job's last step and its (np, 8) particle
+        state (with ``with_mean``: also the (np, 3) mean force over the job's
+        mean window, as the middle item); releases the job's record."""
+        n = max(1, self.np[jid])
+        F = np.zeros((n, 3))
+        Fm = np.zeros((n, 3))
+        st = (Particle * n)()
+        check(self.L.dilbm_server_result(self.h, int(jid), F.ctypes.data, Fm.ctypes.data, C.cast(st, C.c_void_p)))
+        k = self.np.pop(jid)
+        if with_mean:
+            return F[:k], Fm[:k], particles_to_array(st, k)
+        return F[:k], particles_to_array(st, k)
