@@ -115,7 +115,10 @@ int dilbm_create(const dilbm_grid *grid, dilbm_lattice lattice, double tau,
  * 28-29).  Each step is one fused pull-stream + collide sweep over every node,
  * a per-particle FP64 force/torque reduction and a rigid-body update.
  * Asynchronous: returns once the work is queued; errors raised on the device
- * (UNSTABLE, OVERFLOW) surface at the next dilbm_sync().
+ * (UNSTABLE, OVERFLOW) surface at the next dilbm_sync().  Whole pairs of
+ * steps replay a CUDA graph captured on the context's stream on first use
+ * (not on the legacy default stream, not while timing, and not while the
+ * caller is capturing that stream, where the launches are issued directly).
  */
 int dilbm_step(dilbm_ctx *ctx, long long nsteps);
 
@@ -209,6 +212,31 @@ int dilbm_batch_set_timing(dilbm_batch *batch, int enable);
 int dilbm_batch_sweep_time(dilbm_batch *batch, double *ms_total, long long *launches);
 long long dilbm_batch_launch_count(const dilbm_batch *batch);
 void dilbm_batch_destroy(dilbm_batch *batch);
+int dilbm_batch_autotune(dilbm_batch *batch, int reps, int *warps, int *blocks_per_sm);
+int dilbm_batch_set_shape(dilbm_batch *batch, int warps, int blocks_per_sm);
+
+/*
+ * Launch shape of the lattice sweep, and its autotuner.  A shape is the
+ * number of row segments (128 nodes of one row) a block keeps in flight --
+ * warps per block, 2, 4 or 8 -- and the persistent blocks per SM
+ * (blocks_per_sm, 0: as many as fit).  The tile a row segment belongs to
+ * (128 x 8 nodes) is fixed: it orders the force partials.  Every shape runs
+ * the same arithmetic on every node, so results are bit for bit the same in
+ * every shape.
+ *
+ * dilbm_autotune / dilbm_batch_autotune time every candidate shape (each
+ * warps-per-block value with as many blocks per SM as fit and with half as
+ * many) over reps sweep launches of the current state (reps <= 0: 5; the
+ * launches only write what the next step overwrites), keep the fastest and
+ * report it in *warps and *blocks_per_sm (nullable).  The choice is cached
+ * per process, keyed by storage, edge handling and lattice size (for a
+ * batch: storage, member count and total row segments), so tuning a second
+ * context or batch of the same key launches nothing.  Both synchronise.
+ * dilbm_set_shape / dilbm_batch_set_shape set a shape by hand.
+ * Errors: INVALID_ARG, CUDA.
+ */
+int dilbm_autotune(dilbm_ctx *ctx, int reps, int *warps, int *blocks_per_sm);
+int dilbm_set_shape(dilbm_ctx *ctx, int warps, int blocks_per_sm);
 
 /*
  * Device memory dilbm_create allocates for a lattice of grid->nx x grid->ny

@@ -1,13 +1,16 @@
 // C ABI of the DI-LBM library (declared in include/dilbm.h): context
 // management, argument checks, and the launch sequence of one time step.
 #include "dilbm.h"
-#include "dilbm_kernels.cuh"
+#include "dilbm_launch.cuh"
 
 #include <cmath>
 #include <cstdio>
 #include <cstdlib>
 #include <cstring>
+#include <map>
+#include <mutex>
 #include <string>
+#include <tuple>
 #include <vector>
 
 using namespace dilbm;
@@ -60,6 +63,8 @@ struct dilbm_ctx {
     std::vector<cudaEvent_t> ev;      // start/stop pairs around sweep launches
     size_t ev_used = 0;
     long long launches = 0;
+    SweepShape shape{};               // launch shape of the step sweep (autotuned or default)
+    cudaGraphExec_t g_pair[2] = {nullptr, nullptr};   // two steps from parity 0 / 1, replayed by dilbm_step
     void *owned[32] = {};
     int nowned = 0;
 };
@@ -168,8 +173,12 @@ int launch_particles(dilbm_ctx *c, int integrate) {
     return DILBM_OK;
 }
 
+void drop_graphs(dilbm_ctx *c);
+
 int upload_particles(dilbm_ctx *c, const dilbm_particle *p, int np) {
+    const int wx = c->L.wrap_x, wy = c->L.wrap_y;
     set_wrap_flags(c, p, np);
+    if (c->L.wrap_x != wx || c->L.wrap_y != wy) drop_graphs(c);
     int rc = check_reach(c->ph.cut_d, p, np);
     if (rc) return rc;
     std::vector<double> h(8 * (size_t)np);
@@ -208,58 +217,54 @@ SweepArgs<T> sweep_args(const dilbm_ctx *c, int cur, const void *src, void *dst,
     return a;
 }
 
-// Blocks of a sweep kernel resident per SM (queried once per device and
-// kernel) after opting in to its dynamic shared memory.
-template <typename K>
-cudaError_t sweep_occupancy(K kern, int *per_sm_cache, int *per_sm_out) {
-    int dev = 0;
-    cudaError_t e = cudaGetDevice(&dev);
-    if (e != cudaSuccess) return e;
-    if (dev >= 64) return cudaErrorInvalidDevice;
-    if (per_sm_cache[dev] == 0) {
-        const size_t smem = sweep_smem_bytes<float>() > sweep_smem_bytes<__half>() ? sweep_smem_bytes<float>()
-                                                                                    : sweep_smem_bytes<__half>();
-        e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        if (e != cudaSuccess) return e;
-        int n = 0;
-        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, kern, SWEEP_WARPS * 32, smem);
-        if (e != cudaSuccess) return e;
-        per_sm_cache[dev] = n > 0 ? n : 1;
-    }
-    *per_sm_out = per_sm_cache[dev];
-    return cudaSuccess;
-}
-
-// Persistent grid: as many blocks as fit on the device at once, but no more
-// than the row segments need.
-template <typename T, int MODE, bool EDGES>
-cudaError_t launch_sweep_k(dilbm_ctx *c, const void *src, void *dst, FieldsOut fo) {
+// The FIELDS-mode sweep (dilbm_fields) in the default shape.
+template <typename T, bool EDGES>
+cudaError_t launch_fields_sweep(dilbm_ctx *c, const void *src, FieldsOut fo) {
     static int cache[64] = {};
+    constexpr size_t smem = sweep_smem_bytes<T>();
     int per_sm = 1;
-    cudaError_t e = sweep_occupancy(sweep_kernel<T, MODE, EDGES>, cache, &per_sm);
+    cudaError_t e = occupancy_of(sweep_kernel<T, MODE_FIELDS, EDGES>, SWEEP_WARPS, smem, cache, &per_sm);
     if (e != cudaSuccess) return e;
-    const long long items = (long long)c->L.ny * c->L.ntx;
-    long long blocks = (long long)c->num_sms * per_sm;
-    const long long need = (items + SWEEP_WARPS - 1) / SWEEP_WARPS;
-    if (blocks > need) blocks = need;
-    sweep_kernel<T, MODE, EDGES><<<(unsigned)blocks, SWEEP_WARPS * 32, sweep_smem_bytes<T>(), c->stream>>>(
-        sweep_args<T>(c, c->cur, src, dst, MODE == MODE_STEP, fo));
+    const long long blocks = persistent_grid((long long)c->L.ny * c->L.ntx, SWEEP_WARPS, per_sm, c->num_sms, SweepShape{});
+    sweep_kernel<T, MODE_FIELDS, EDGES><<<(unsigned)blocks, SWEEP_WARPS * 32, smem, c->stream>>>(
+        sweep_args<T>(c, c->cur, src, nullptr, false, fo));
     return cudaGetLastError();
 }
 
-template <typename T, int MODE>
-cudaError_t launch_sweep_t(dilbm_ctx *c, const void *src, void *dst, FieldsOut fo) {
-    if (c->L.per_x && c->L.per_y) return launch_sweep_k<T, MODE, false>(c, src, dst, fo);
-    return launch_sweep_k<T, MODE, true>(c, src, dst, fo);
+bool has_edges(const dilbm_ctx *c) { return !(c->L.per_x && c->L.per_y); }
+
+// The step sweep of the current parity in shape `sh` (query: occupancy only).
+cudaError_t step_sweep(dilbm_ctx *c, const SweepShape &sh, bool query = false, int *per_sm = nullptr) {
+    const void *src = c->buf[c->cur];
+    void *dst = c->buf[c->cur ^ 1];
+    const bool edges = has_edges(c);
+    switch (c->storage) {
+    case DILBM_FP32:
+        return launch_step_sweep<float>(sweep_args<float>(c, c->cur, src, dst, true, FieldsOut{}), edges, sh,
+                                        c->num_sms, c->stream, query, per_sm);
+    case DILBM_FP16_DEV:
+        return launch_step_sweep<__half>(sweep_args<__half>(c, c->cur, src, dst, true, FieldsOut{}), edges, sh,
+                                         c->num_sms, c->stream, query, per_sm);
+    default:
+        return launch_step_sweep<__nv_bfloat16>(sweep_args<__nv_bfloat16>(c, c->cur, src, dst, true, FieldsOut{}),
+                                                edges, sh, c->num_sms, c->stream, query, per_sm);
+    }
 }
 
 template <int MODE>
 int launch_sweep(dilbm_ctx *c, const void *src, void *dst, FieldsOut fo) {
     cudaError_t e;
-    switch (c->storage) {
-    case DILBM_FP32: e = launch_sweep_t<float, MODE>(c, src, dst, fo); break;
-    case DILBM_FP16_DEV: e = launch_sweep_t<__half, MODE>(c, src, dst, fo); break;
-    default: e = launch_sweep_t<__nv_bfloat16, MODE>(c, src, dst, fo); break;
+    if (MODE == MODE_STEP) {
+        (void)src;
+        (void)dst;
+        e = step_sweep(c, c->shape);
+    } else {
+        const bool edges = has_edges(c);
+        switch (c->storage) {
+        case DILBM_FP32: e = edges ? launch_fields_sweep<float, true>(c, src, fo) : launch_fields_sweep<float, false>(c, src, fo); break;
+        case DILBM_FP16_DEV: e = edges ? launch_fields_sweep<__half, true>(c, src, fo) : launch_fields_sweep<__half, false>(c, src, fo); break;
+        default: e = edges ? launch_fields_sweep<__nv_bfloat16, true>(c, src, fo) : launch_fields_sweep<__nv_bfloat16, false>(c, src, fo); break;
+        }
     }
     if (e != cudaSuccess) return cuda_fail(e, "sweep_kernel launch");
     c->launches += 1;
@@ -287,6 +292,43 @@ int one_step(dilbm_ctx *c) {
     if (c->np > 0 && (rc = launch_particles(c, 1))) return rc;
     c->cur ^= 1;
     c->fsum_steps += 1;
+    return DILBM_OK;
+}
+
+void drop_graphs(dilbm_ctx *c) {
+    for (int p = 0; p < 2; ++p)
+        if (c->g_pair[p]) {
+            cudaGraphExecDestroy(c->g_pair[p]);
+            c->g_pair[p] = nullptr;
+        }
+}
+
+// Two steps starting at parity p, captured into a graph on the context's
+// stream (nothing runs while capturing).
+int capture_pair(dilbm_ctx *c, int p) {
+    if (c->g_pair[p]) return DILBM_OK;
+    const int cur = c->cur;
+    const long long l0 = c->launches, f0 = c->fsum_steps;
+    c->cur = p;
+    cudaGraph_t g = nullptr;
+    DILBM_CUDA(cudaStreamBeginCapture(c->stream, cudaStreamCaptureModeThreadLocal));
+    int rc = one_step(c);
+    if (rc == DILBM_OK) rc = one_step(c);
+    const cudaError_t e = cudaStreamEndCapture(c->stream, &g);
+    c->cur = cur;
+    c->launches = l0;
+    c->fsum_steps = f0;
+    if (rc) {
+        if (g) cudaGraphDestroy(g);
+        return rc;
+    }
+    if (e != cudaSuccess) return cuda_fail(e, "cudaStreamEndCapture");
+    const cudaError_t e2 = cudaGraphInstantiate(&c->g_pair[p], g, 0);
+    cudaGraphDestroy(g);
+    if (e2 != cudaSuccess) {
+        c->g_pair[p] = nullptr;
+        return cuda_fail(e2, "cudaGraphInstantiate");
+    }
     return DILBM_OK;
 }
 
@@ -382,6 +424,22 @@ int dilbm_create(const dilbm_grid *g, dilbm_lattice lattice, double tau, double 
         L.side_uy[k] = (float)sides[k]->uy;
         L.side_drho[k] = (float)(sides[k]->rho - 1.0);
     }
+    // 16-bit storage: deviations from the initial equilibrium f^eq(rho_init,
+    // u0) (Eq. 2), scaled by 2^14 in FP16 so that small values stay normal
+    {
+        const double w[9] = {4.0 / 9, 1.0 / 9, 1.0 / 9, 1.0 / 9, 1.0 / 9, 1.0 / 36, 1.0 / 36, 1.0 / 36, 1.0 / 36};
+        const bool wide = g->storage == DILBM_FP32;
+        const double q = g->storage == DILBM_FP16_DEV ? 1.0 / 16384.0 : 1.0;
+        const double r0 = g->rho_init, ux = g->u0[0], uy = g->u0[1];
+        for (int i = 0; i < 9; ++i) {
+            const double cu = cxof(i) * ux + cyof(i) * uy;
+            const double e = w[i] * r0 * (1.0 + 3.0 * cu + 4.5 * cu * cu - 1.5 * (ux * ux + uy * uy)) - w[i];
+            L.ref_e[i] = wide ? 0.0f : (float)e;
+            L.ref_ne[i] = wide ? 0.0f : (float)(-(double)L.ref_e[i] / q);
+        }
+        L.ref_q = (float)q;
+        L.ref_iq = (float)(1.0 / q);
+    }
     c->ntiles = L.ntx * L.nty;
     Physics &ph = c->ph;
     ph.omega = (float)(1.0 / tau);
@@ -466,7 +524,23 @@ int dilbm_create(const dilbm_grid *g, dilbm_lattice lattice, double tau, double 
 
 int dilbm_step(dilbm_ctx *c, long long nsteps) {
     if (!c || nsteps < 0) return fail(DILBM_ERR_INVALID_ARG, "bad context or step count");
-    for (long long t = 0; t < nsteps; ++t) {
+    // whole step pairs replay a captured graph (timing brackets every sweep
+    // launch with events instead; a stream the caller is capturing gets the
+    // launches themselves)
+    bool graphs = !c->timing && nsteps >= 2 && c->stream != nullptr && c->stream != cudaStreamLegacy;
+    if (graphs) {
+        cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+        graphs = cudaStreamIsCapturing(c->stream, &cs) == cudaSuccess && cs == cudaStreamCaptureStatusNone;
+    }
+    long long t = 0;
+    if (graphs) {
+        int rc = capture_pair(c, c->cur);
+        if (rc) return rc;
+        for (; t + 2 <= nsteps; t += 2) DILBM_CUDA(cudaGraphLaunch(c->g_pair[c->cur], c->stream));
+        c->launches += t * (c->np > 0 ? 2 : 1);
+        c->fsum_steps += t;
+    }
+    for (; t < nsteps; ++t) {
         int rc = one_step(c);
         if (rc) return rc;
     }
@@ -605,6 +679,7 @@ int dilbm_set_particles(dilbm_ctx *c, const dilbm_particle *p, int np) {
 void dilbm_destroy(dilbm_ctx *c) {
     if (!c) return;
     cudaStreamSynchronize(c->stream);
+    drop_graphs(c);
     for (int k = 0; k < c->nowned; ++k) cudaFree(c->owned[k]);
     for (cudaEvent_t e : c->ev) cudaEventDestroy(e);
     delete c;
@@ -662,7 +737,7 @@ struct dilbm_batch {
     int *err_out = nullptr;             // device: their values, gathered for one copy
     std::vector<int> err_host;
     int nparts = 0;
-    std::vector<int> group_blocks;      // persistent grid of each launch group
+    SweepShape shape{};                 // launch shape of the batched sweep
     cudaGraphExec_t g_pair = nullptr, g_single[2] = {nullptr, nullptr};
     bool timing = false;
     std::vector<cudaEvent_t> ev;
@@ -694,10 +769,8 @@ template <typename T>
 void build_sweep_params(dilbm_batch *b) {
     free_sweep_params(b);
     const int n = (int)b->members.size();
-    b->group_blocks.clear();
     for (int g0 = 0; g0 < n; g0 += BATCH_LAUNCH_MAX) {
         const int gn = n - g0 < BATCH_LAUNCH_MAX ? n - g0 : BATCH_LAUNCH_MAX;
-        int items = 0;
         for (int phase = 0; phase < 2; ++phase) {
             BatchArgs<T> *ba = static_cast<BatchArgs<T> *>(std::calloc(1, sizeof(BatchArgs<T>)));
             ba->n = gn;
@@ -709,10 +782,8 @@ void build_sweep_params(dilbm_batch *b) {
                 ba->item_start[k + 1] = ba->item_start[k] + c->L.ny * c->L.ntx;
                 ba->tile_start[k + 1] = ba->tile_start[k] + c->L.ntx * c->L.nty;
             }
-            items = ba->item_start[gn];
             b->sweep_params[phase].push_back(ba);
         }
-        b->group_blocks.push_back(items);    // converted to a grid size by the caller
     }
 }
 
@@ -728,14 +799,21 @@ int upload_part_args(dilbm_batch *b) {
 }
 
 template <typename T>
-cudaError_t launch_batch_sweep(dilbm_batch *b, int phase) {
+cudaError_t batch_sweep_groups(dilbm_batch *b, int phase, const SweepShape &sh) {
+    const int num_sms = b->members[0]->num_sms;
     for (size_t g = 0; g < b->sweep_params[phase].size(); ++g) {
         const BatchArgs<T> &ba = *static_cast<const BatchArgs<T> *>(b->sweep_params[phase][g]);
-        sweep_batch_kernel<T, MODE_STEP><<<b->group_blocks[g], SWEEP_WARPS * 32, sweep_smem_bytes<T>(), b->stream>>>(ba);
-        cudaError_t e = cudaGetLastError();
+        cudaError_t e = launch_batch_sweep<T>(ba, sh, num_sms, b->stream);
         if (e != cudaSuccess) return e;
     }
     return cudaSuccess;
+}
+
+// Every launch group of the batched sweep at `phase` in shape `sh`.
+cudaError_t batch_sweep(dilbm_batch *b, int phase, const SweepShape &sh) {
+    if (b->storage == DILBM_FP32) return batch_sweep_groups<float>(b, phase, sh);
+    if (b->storage == DILBM_FP16_DEV) return batch_sweep_groups<__half>(b, phase, sh);
+    return batch_sweep_groups<__nv_bfloat16>(b, phase, sh);
 }
 
 // One batch step at `phase`: the sweep over every member, then the particles.
@@ -753,10 +831,7 @@ int batch_phase(dilbm_batch *b, int phase) {
         b->ev_used += 2;
         DILBM_CUDA(cudaEventRecord(e0, b->stream));
     }
-    cudaError_t e;
-    if (b->storage == DILBM_FP32) e = launch_batch_sweep<float>(b, phase);
-    else if (b->storage == DILBM_FP16_DEV) e = launch_batch_sweep<__half>(b, phase);
-    else e = launch_batch_sweep<__nv_bfloat16>(b, phase);
+    cudaError_t e = batch_sweep(b, phase, b->shape);
     if (e != cudaSuccess) return cuda_fail(e, "batched sweep_kernel launch");
     if (b->timing) DILBM_CUDA(cudaEventRecord(e1, b->stream));
     b->launches += (long long)b->sweep_params[phase].size();
@@ -800,18 +875,6 @@ int prepare_batch(dilbm_batch *b) {
     if (b->storage == DILBM_FP32) build_sweep_params<float>(b);
     else if (b->storage == DILBM_FP16_DEV) build_sweep_params<__half>(b);
     else build_sweep_params<__nv_bfloat16>(b);
-    static int cache32[64] = {}, cache16[64] = {}, cacheb[64] = {};
-    int per_sm = 1;
-    cudaError_t e;
-    if (b->storage == DILBM_FP32) e = sweep_occupancy(sweep_batch_kernel<float, MODE_STEP>, cache32, &per_sm);
-    else if (b->storage == DILBM_FP16_DEV) e = sweep_occupancy(sweep_batch_kernel<__half, MODE_STEP>, cache16, &per_sm);
-    else e = sweep_occupancy(sweep_batch_kernel<__nv_bfloat16, MODE_STEP>, cacheb, &per_sm);
-    if (e != cudaSuccess) return cuda_fail(e, "batched sweep occupancy");
-    for (int &items : b->group_blocks) {
-        const long long full = (long long)b->members[0]->num_sms * per_sm;
-        const long long need = (items + SWEEP_WARPS - 1) / SWEEP_WARPS;
-        items = (int)(need < full ? (need > 0 ? need : 1) : full);
-    }
     int rc;
     if ((rc = upload_part_args(b))) return rc;
     if ((rc = capture(b, 0, 2, &b->g_pair)) || (rc = capture(b, 0, 1, &b->g_single[0])) ||
@@ -1000,6 +1063,166 @@ void dilbm_batch_destroy(dilbm_batch *b) {
     if (b->ev_out) cudaEventDestroy(b->ev_out);
     if (b->stream) cudaStreamDestroy(b->stream);
     delete b;
+}
+
+}  // extern "C"
+
+// ---------------------------------------------------------------- autotuner
+// Picks the sweep's launch shape (rows in flight per block, blocks per SM) by
+// timing each candidate on the caller's own state.  Shapes do not change the
+// arithmetic, so the choice is free to follow the clock.
+namespace {
+
+std::mutex g_tune_mu;
+std::map<std::tuple<int, int, int, long long, long long>, SweepShape> g_tune;
+
+template <typename Occ>
+int shape_candidates(Occ occupancy, std::vector<SweepShape> *out) {
+    for (int w : SHAPE_WARPS) {
+        int per_sm = 0;
+        cudaError_t e = occupancy(SweepShape{w, 0}, &per_sm);
+        if (e != cudaSuccess) return cuda_fail(e, "sweep occupancy");
+        out->push_back(SweepShape{w, per_sm});
+        if (per_sm >= 2) out->push_back(SweepShape{w, per_sm / 2});
+    }
+    return DILBM_OK;
+}
+
+// Time `reps` launches of each candidate (after one untimed launch) on
+// `stream`; *best receives the fastest.
+template <typename Launch>
+int time_shapes(cudaStream_t stream, int reps, const std::vector<SweepShape> &cands, Launch launch, SweepShape *best) {
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    DILBM_CUDA(cudaEventCreate(&e0));
+    cudaError_t e = cudaEventCreate(&e1);
+    if (e != cudaSuccess) {
+        cudaEventDestroy(e0);
+        return cuda_fail(e, "cudaEventCreate");
+    }
+    float best_ms = 0.f;
+    int rc = DILBM_OK;
+    for (size_t k = 0; k < cands.size() && rc == DILBM_OK; ++k) {
+        float ms = 0.f;
+        e = launch(cands[k]);
+        if (e == cudaSuccess) e = cudaEventRecord(e0, stream);
+        for (int r = 0; r < reps && e == cudaSuccess; ++r) e = launch(cands[k]);
+        if (e == cudaSuccess) e = cudaEventRecord(e1, stream);
+        if (e == cudaSuccess) e = cudaEventSynchronize(e1);
+        if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
+        if (e != cudaSuccess) rc = cuda_fail(e, "autotune launch");
+        else if (k == 0 || ms < best_ms) {
+            best_ms = ms;
+            *best = cands[k];
+        }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    return rc;
+}
+
+bool tuned(const std::tuple<int, int, int, long long, long long> &key, SweepShape *out) {
+    std::lock_guard<std::mutex> lk(g_tune_mu);
+    auto it = g_tune.find(key);
+    if (it == g_tune.end()) return false;
+    *out = it->second;
+    return true;
+}
+
+void remember(const std::tuple<int, int, int, long long, long long> &key, const SweepShape &sh) {
+    std::lock_guard<std::mutex> lk(g_tune_mu);
+    g_tune[key] = sh;
+}
+
+void report_shape(const SweepShape &sh, int *warps, int *blocks_per_sm) {
+    if (warps) *warps = sh.warps;
+    if (blocks_per_sm) *blocks_per_sm = sh.blocks_per_sm;
+}
+
+}  // namespace
+
+extern "C" {
+
+int dilbm_set_shape(dilbm_ctx *c, int warps, int blocks_per_sm) {
+    const SweepShape sh{warps, blocks_per_sm};
+    if (!c || !shape_valid(sh)) return fail(DILBM_ERR_INVALID_ARG, "warps must be 2, 4 or 8 and blocks_per_sm >= 0");
+    if (sh.warps != c->shape.warps || sh.blocks_per_sm != c->shape.blocks_per_sm) {
+        DILBM_CUDA(cudaStreamSynchronize(c->stream));
+        drop_graphs(c);
+        c->shape = sh;
+    }
+    return DILBM_OK;
+}
+
+int dilbm_autotune(dilbm_ctx *c, int reps, int *warps, int *blocks_per_sm) {
+    if (!c) return fail(DILBM_ERR_INVALID_ARG, "NULL context");
+    if (reps <= 0) reps = 5;
+    const auto key = std::make_tuple(0, c->storage, has_edges(c) ? 1 : 0, (long long)c->L.nx, (long long)c->L.ny);
+    SweepShape best = c->shape;
+    if (!tuned(key, &best)) {
+        std::vector<SweepShape> cands;
+        int rc = shape_candidates([&](const SweepShape &sh, int *per_sm) { return step_sweep(c, sh, true, per_sm); },
+                                  &cands);
+        if (rc) return rc;
+        // each launch sweeps the current state into the other buffer: what
+        // the next step writes anyway
+        rc = time_shapes(c->stream, reps, cands, [&](const SweepShape &sh) { return step_sweep(c, sh); }, &best);
+        c->launches += (long long)cands.size() * (reps + 1);
+        if (rc) return rc;
+        remember(key, best);
+    }
+    report_shape(best, warps, blocks_per_sm);
+    return dilbm_set_shape(c, best.warps, best.blocks_per_sm);
+}
+
+int dilbm_batch_set_shape(dilbm_batch *b, int warps, int blocks_per_sm) {
+    const SweepShape sh{warps, blocks_per_sm};
+    if (!b || !shape_valid(sh)) return fail(DILBM_ERR_INVALID_ARG, "warps must be 2, 4 or 8 and blocks_per_sm >= 0");
+    if (sh.warps == b->shape.warps && sh.blocks_per_sm == b->shape.blocks_per_sm) return DILBM_OK;
+    DILBM_CUDA(cudaStreamSynchronize(b->stream));
+    b->shape = sh;
+    return prepare_batch(b);     // re-capture the graphs in the new shape
+}
+
+int dilbm_batch_autotune(dilbm_batch *b, int reps, int *warps, int *blocks_per_sm) {
+    if (!b) return fail(DILBM_ERR_INVALID_ARG, "NULL batch");
+    if (reps <= 0) reps = 5;
+    long long items = 0;
+    for (const dilbm_ctx *c : b->members) items += (long long)c->L.ny * c->L.ntx;
+    const auto key = std::make_tuple(1, b->storage, (int)b->members.size(), items, 0LL);
+    SweepShape best = b->shape;
+    if (!tuned(key, &best)) {
+        cudaError_t e;
+        // order after the members' queued work; bring the launches up to date
+        for (cudaStream_t s : b->member_streams)
+            if ((e = cudaEventRecord(b->ev_in, s)) != cudaSuccess || (e = cudaStreamWaitEvent(b->stream, b->ev_in, 0)) != cudaSuccess)
+                return cuda_fail(e, "batch stream ordering");
+        bool stale = false;
+        for (size_t k = 0; k < b->members.size(); ++k)
+            stale |= b->members[k]->cur != (b->cur0[k] ^ (int)(b->done & 1));
+        int rc;
+        if (stale && (rc = prepare_batch(b))) return rc;
+        const int phase = (int)(b->done & 1);
+        std::vector<SweepShape> cands;
+        rc = shape_candidates(
+            [&](const SweepShape &sh, int *per_sm) {
+                switch (b->storage) {
+                case DILBM_FP32: return launch_batch_sweep<float>(*static_cast<const BatchArgs<float> *>(b->sweep_params[0][0]), sh, 1, b->stream, true, per_sm);
+                case DILBM_FP16_DEV: return launch_batch_sweep<__half>(*static_cast<const BatchArgs<__half> *>(b->sweep_params[0][0]), sh, 1, b->stream, true, per_sm);
+                default: return launch_batch_sweep<__nv_bfloat16>(*static_cast<const BatchArgs<__nv_bfloat16> *>(b->sweep_params[0][0]), sh, 1, b->stream, true, per_sm);
+                }
+            },
+            &cands);
+        if (rc) return rc;
+        rc = time_shapes(b->stream, reps, cands, [&](const SweepShape &sh) { return batch_sweep(b, phase, sh); }, &best);
+        b->launches += (long long)cands.size() * (reps + 1) * (long long)b->sweep_params[phase].size();
+        if (rc) return rc;
+        remember(key, best);
+        if ((e = cudaEventRecord(b->ev_out, b->stream)) != cudaSuccess) return cuda_fail(e, "cudaEventRecord");
+        for (cudaStream_t s : b->member_streams)
+            if ((e = cudaStreamWaitEvent(s, b->ev_out, 0)) != cudaSuccess) return cuda_fail(e, "cudaStreamWaitEvent");
+    }
+    report_shape(best, warps, blocks_per_sm);
+    return dilbm_batch_set_shape(b, best.warps, best.blocks_per_sm);
 }
 
 }  // extern "C"

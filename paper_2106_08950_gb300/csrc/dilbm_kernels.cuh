@@ -27,6 +27,7 @@
 #pragma once
 
 #include <cuda_bf16.h>
+#include <type_traits>
 #include <cuda_fp16.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
@@ -40,7 +41,7 @@ constexpr int MAXC = 32;      // candidate particles per tile
 constexpr int MAXT = 128;     // tiles one particle's phi tail may reach
 constexpr int NREC = 3;       // float4 records per binned particle
 constexpr int STAGES = 2;     // shared-memory ring depth per warp
-constexpr int SWEEP_WARPS = 8;
+constexpr int SWEEP_WARPS = 8;   // default rows in flight per block (one row segment per warp)
 constexpr int GUARD = 256;    // elements kept readable before and after a population buffer
 constexpr float PHI_CUT_WIDTHS = 4.0f;   // phi tail kept up to 4 interface widths (phi > 1.1e-7)
 constexpr unsigned long long WAIT_LIMIT_NS = 1000000000ull;   // bounded device waits: 1 s
@@ -111,12 +112,12 @@ template <> struct Storage<__nv_bfloat16> {
 template <typename T> __host__ __device__ constexpr int halo_of() { return 16 / (int)sizeof(T); }
 template <typename T> __host__ __device__ constexpr int segw_of() { return TILE_W + 2 * halo_of<T>(); }
 
-// Dynamic shared memory of one sweep block.
-template <typename T> __host__ __device__ constexpr size_t sweep_smem_bytes() {
-    return (size_t)SWEEP_WARPS * STAGES * 9 * segw_of<T>() * sizeof(T)   // staged rows
-           + (size_t)SWEEP_WARPS * MAXC * NREC * sizeof(float4)           // candidate records
-           + (size_t)SWEEP_WARPS * MAXC * sizeof(int)                     // candidate ids
-           + (size_t)SWEEP_WARPS * STAGES * sizeof(uint64_t);             // mbarriers
+// Dynamic shared memory of one sweep block of W warps.
+template <typename T, int W = SWEEP_WARPS> __host__ __device__ constexpr size_t sweep_smem_bytes() {
+    return (size_t)W * STAGES * 9 * segw_of<T>() * sizeof(T)   // staged rows
+           + (size_t)W * MAXC * NREC * sizeof(float4)           // candidate records
+           + (size_t)W * MAXC * sizeof(int)                     // candidate ids
+           + (size_t)W * STAGES * sizeof(uint64_t);             // mbarriers
 }
 
 // ------------------------------------------------------------ parameters
@@ -136,7 +137,43 @@ struct Lattice {
                                 // need their own minimum image
     int side_kind[4];
     float side_ux[4], side_uy[4], side_drho[4];   // drho = rho_b - 1
+    // 16-bit storage holds s_i = (d_i - e_i) / q: d_i = f_i - w_i the FP32
+    // deviation, e_i the deviation of the lattice's initial equilibrium
+    // f^eq(rho_init, u0) and q a power of two that keeps small s_i out of
+    // the FP16 subnormals.  FP32 storage holds d_i itself.
+    float ref_e[9];             // e_i
+    float ref_ne[9];            // -e_i / q
+    float ref_q, ref_iq;        // q, 1 / q
 };
+
+// Stored value <-> FP32 deviation d_i for direction i (exact scalings by a
+// power of two, one rounding in the offset).
+template <typename T> __device__ __forceinline__ float from_store(const Lattice &L, int i, float v) {
+    if constexpr (std::is_same<T, float>::value) return v;
+    else return fmaf(v, L.ref_q, L.ref_e[i]);
+}
+template <typename T> __device__ __forceinline__ float to_store(const Lattice &L, int i, float d) {
+    if constexpr (std::is_same<T, float>::value) return d;
+    else return fmaf(d, L.ref_iq, L.ref_ne[i]);
+}
+template <typename T> __device__ __forceinline__ float4 from_store4(const Lattice &L, int i, float4 v) {
+    if constexpr (std::is_same<T, float>::value) {
+        return v;
+    } else {
+        const float2 q = make_float2(L.ref_q, L.ref_q), e = make_float2(L.ref_e[i], L.ref_e[i]);
+        const float2 a = __ffma2_rn(make_float2(v.x, v.y), q, e), b = __ffma2_rn(make_float2(v.z, v.w), q, e);
+        return make_float4(a.x, a.y, b.x, b.y);
+    }
+}
+template <typename T> __device__ __forceinline__ float4 to_store4(const Lattice &L, int i, float4 d) {
+    if constexpr (std::is_same<T, float>::value) {
+        return d;
+    } else {
+        const float2 q = make_float2(L.ref_iq, L.ref_iq), e = make_float2(L.ref_ne[i], L.ref_ne[i]);
+        const float2 a = __ffma2_rn(make_float2(d.x, d.y), q, e), b = __ffma2_rn(make_float2(d.z, d.w), q, e);
+        return make_float4(a.x, a.y, b.x, b.y);
+    }
+}
 
 struct Physics {
     float omega;                // 1 / tau
@@ -396,7 +433,7 @@ __device__ __forceinline__ void pull_node_scalar(const T *__restrict__ src, cons
     for (int i = 0; i < 9; ++i) {
         int sx = wrap_or_clamp(x - cxof(i), L.nx, L.per_x);
         int sy = wrap_or_clamp(y - cyof(i), L.ny, L.per_y);
-        d[i] = Storage<T>::load1(src + i * L.plane + (long long)sy * L.pitch + sx);
+        d[i] = from_store<T>(L, i, Storage<T>::load1(src + i * L.plane + (long long)sy * L.pitch + sx));
     }
 }
 
@@ -482,7 +519,7 @@ struct SweepArgs {
 // held in the kernel's parameter space (uniform constant-cache reads, no
 // aliasing with the stores): lattice k owns row segments
 // [item_start[k], item_start[k+1]) and tiles [tile_start[k], tile_start[k+1]).
-constexpr int BATCH_LAUNCH_MAX = 96;     // lattices per batched launch
+constexpr int BATCH_LAUNCH_MAX = 88;     // lattices per batched launch
 
 template <typename T>
 struct BatchArgs {
@@ -554,14 +591,11 @@ __device__ __forceinline__ bool sweep_segment(const SweepArgs<T> &A, int y, int 
     float d[9][VEC];
 #pragma unroll
     for (int i = 0; i < 9; ++i) {
-        const float4 v = Storage<T>::lds4(stage + i * SW + c0);
-        if (cxof(i) == 0) {
-            d[i][0] = v.x; d[i][1] = v.y; d[i][2] = v.z; d[i][3] = v.w;
-        } else if (cxof(i) == 1) {
-            d[i][0] = Storage<T>::lds1(stage + i * SW + c0 - 1); d[i][1] = v.x; d[i][2] = v.y; d[i][3] = v.z;
-        } else {
-            d[i][0] = v.y; d[i][1] = v.z; d[i][2] = v.w; d[i][3] = Storage<T>::lds1(stage + i * SW + c0 + VEC);
-        }
+        float4 v = Storage<T>::lds4(stage + i * SW + c0);
+        if (cxof(i) == 1) v = make_float4(Storage<T>::lds1(stage + i * SW + c0 - 1), v.x, v.y, v.z);
+        else if (cxof(i) == -1) v = make_float4(v.y, v.z, v.w, Storage<T>::lds1(stage + i * SW + c0 + VEC));
+        v = from_store4<T>(L, i, v);
+        d[i][0] = v.x; d[i][1] = v.y; d[i][2] = v.z; d[i][3] = v.w;
     }
     __syncwarp();
     // recycle the stage for the segment STAGES items ahead
@@ -578,12 +612,12 @@ __device__ __forceinline__ bool sweep_segment(const SweepArgs<T> &A, int y, int 
             if (cxof(i) == 0) continue;
             const int sy = wrap_or_clamp(y - cyof(i), L.ny, L.per_y);
             const T *row = A.src + i * L.plane + (long long)sy * L.pitch;
-            if (cxof(i) == 1 && x0 == 0) d[i][0] = Storage<T>::load1(row + (L.nx - 1));
+            if (cxof(i) == 1 && x0 == 0) d[i][0] = from_store<T>(L, i, Storage<T>::load1(row + (L.nx - 1)));
             if (cxof(i) == -1) {
                 const int kl = L.nx - 1 - x0;
 #pragma unroll
                 for (int q = 0; q < VEC; ++q)
-                    if (q == kl) d[i][q] = Storage<T>::load1(row);
+                    if (q == kl) d[i][q] = from_store<T>(L, i, Storage<T>::load1(row));
             }
         }
     }
@@ -778,12 +812,14 @@ __device__ __forceinline__ bool sweep_segment(const SweepArgs<T> &A, int y, int 
 #pragma unroll
         for (int i = 0; i < 9; ++i) {
             T *row = A.dst + i * L.plane + (long long)y * L.pitch;
+            const float4 v = to_store4<T>(L, i, make_float4(d[i][0], d[i][1], d[i][2], d[i][3]));
             if (full) {
-                Storage<T>::store4(row + x0, make_float4(d[i][0], d[i][1], d[i][2], d[i][3]));
+                Storage<T>::store4(row + x0, v);
             } else {
+                const float vv[VEC] = {v.x, v.y, v.z, v.w};
 #pragma unroll
                 for (int q = 0; q < VEC; ++q)
-                    if (x0 + q < L.nx) Storage<T>::store1(row + x0 + q, d[i][q]);
+                    if (x0 + q < L.nx) Storage<T>::store1(row + x0 + q, vv[q]);
             }
         }
     }
@@ -814,7 +850,7 @@ __device__ __forceinline__ bool sweep_segment(const SweepArgs<T> &A, int y, int 
 }
 
 // Shared-memory carve-up common to both sweep kernels.
-template <typename T>
+template <typename T, int W>
 struct SweepSmem {
     T *stages;
     float4 *crec;
@@ -822,9 +858,9 @@ struct SweepSmem {
     uint64_t *bars;
     __device__ __forceinline__ SweepSmem(unsigned char *raw, int warp) {
         constexpr int SW = segw_of<T>();
-        constexpr size_t STAGE_BYTES = (size_t)SWEEP_WARPS * STAGES * 9 * SW * sizeof(T);
-        constexpr size_t REC_BYTES = (size_t)SWEEP_WARPS * NREC * MAXC * sizeof(float4);
-        constexpr size_t ID_BYTES = (size_t)SWEEP_WARPS * MAXC * sizeof(int);
+        constexpr size_t STAGE_BYTES = (size_t)W * STAGES * 9 * SW * sizeof(T);
+        constexpr size_t REC_BYTES = (size_t)W * NREC * MAXC * sizeof(float4);
+        constexpr size_t ID_BYTES = (size_t)W * MAXC * sizeof(int);
         stages = reinterpret_cast<T *>(raw) + (size_t)warp * STAGES * 9 * SW;
         crec = reinterpret_cast<float4 *>(raw + STAGE_BYTES) + (size_t)warp * NREC * MAXC;
         cid = reinterpret_cast<int *>(raw + STAGE_BYTES + REC_BYTES) + warp * MAXC;
@@ -834,15 +870,16 @@ struct SweepSmem {
 
 // The sweep over one lattice.  Persistent: warps take row segments
 // round-robin (neighbouring warps on neighbouring segments); each warp keeps
-// STAGES segments staged ahead.
-template <typename T, int MODE, bool EDGES>
-__global__ void __launch_bounds__(SWEEP_WARPS * 32, 2)
+// STAGES segments staged ahead.  W warps per block (rows in flight per
+// block); every W caps registers at 128 per thread.
+template <typename T, int MODE, bool EDGES, int W = SWEEP_WARPS>
+__global__ void __launch_bounds__(W * 32, 16 / W)
 sweep_kernel(const __grid_constant__ SweepArgs<T> one)
 {
     constexpr int SW = segw_of<T>();
     extern __shared__ __align__(128) unsigned char smem_raw[];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    SweepSmem<T> sm(smem_raw, warp);
+    SweepSmem<T, W> sm(smem_raw, warp);
     Ring ring;
     ring.bars = sm.bars;
     if (lane == 0) {
@@ -857,7 +894,7 @@ sweep_kernel(const __grid_constant__ SweepArgs<T> one)
             one.clear[t] = 0;
 
     const int nitems = L.ny * L.ntx;
-    const int gw = blockIdx.x * SWEEP_WARPS + warp, nw = gridDim.x * SWEEP_WARPS;
+    const int gw = blockIdx.x * W + warp, nw = gridDim.x * W;
     // item = y * ntx + tx, advanced by nw per iteration without dividing
     const int dy_step = nw / L.ntx, dtx_step = nw - dy_step * L.ntx;
     auto advance = [&](int &yy, int &xx) {
@@ -926,14 +963,14 @@ __device__ __forceinline__ void cursor_seek(const BatchArgs<T> &ba, Cursor &c, i
 // single-lattice sweep, so that neighbouring warps stage neighbouring rows
 // (DRAM page locality); each item finds its lattice by a binary search in the
 // parameter space.
-template <typename T, int MODE>
-__global__ void __launch_bounds__(SWEEP_WARPS * 32, 2)
+template <typename T, int MODE, int W = SWEEP_WARPS>
+__global__ void __launch_bounds__(W * 32, 16 / W)
 sweep_batch_kernel(const __grid_constant__ BatchArgs<T> ba)
 {
     constexpr int SW = segw_of<T>();
     extern __shared__ __align__(128) unsigned char smem_raw[];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    SweepSmem<T> sm(smem_raw, warp);
+    SweepSmem<T, W> sm(smem_raw, warp);
     Ring ring;
     ring.bars = sm.bars;
     if (lane == 0) {
@@ -950,7 +987,7 @@ sweep_batch_kernel(const __grid_constant__ BatchArgs<T> ba)
     }
 
     const int nitems = ba.item_start[ba.n];
-    const int gw = blockIdx.x * SWEEP_WARPS + warp, nw = gridDim.x * SWEEP_WARPS;
+    const int gw = blockIdx.x * W + warp, nw = gridDim.x * W;
     Cursor cur, ahead;
     ring.parity = 0;
     ring.pending = 0;
@@ -1238,6 +1275,16 @@ __global__ void particles_kernel(const __grid_constant__ PartArgs one, const Par
 }
 
 // ------------------------------------------------------------ conversions
+// e_i of direction i given at run time (the conversion kernels index by a
+// computed direction).
+__device__ __forceinline__ float ref_e_of(const Lattice &L, int i) {
+    float v = L.ref_e[0];
+#pragma unroll
+    for (int j = 1; j < 9; ++j)
+        if (i == j) v = L.ref_e[j];
+    return v;
+}
+
 // Populations <-> FP64 f_i (dense 9 x ny x nx) for checkpoints.
 template <typename T>
 __global__ void export_kernel(const T *__restrict__ src, Lattice L, double *__restrict__ out) {
@@ -1246,7 +1293,8 @@ __global__ void export_kernel(const T *__restrict__ src, Lattice L, double *__re
         const int i = (int)(k / n);
         const long long r = k - i * n;
         const int y = (int)(r / L.nx), x = (int)(r - (long long)y * L.nx);
-        out[k] = (double)Storage<T>::load1(src + i * L.plane + (long long)y * L.pitch + x) + (double)wof(i);
+        const double v = (double)Storage<T>::load1(src + i * L.plane + (long long)y * L.pitch + x);
+        out[k] = (std::is_same<T, float>::value ? v : v * (double)L.ref_q + (double)ref_e_of(L, i)) + (double)wof(i);
     }
 }
 
@@ -1260,7 +1308,10 @@ __global__ void import_kernel(T *__restrict__ dst, Lattice L, const double *__re
         const int i = (int)(k / n);
         const long long r = k - i * n;
         const int y = (int)(r / L.nx), x = (int)(r - (long long)y * L.nx);
-        Storage<T>::store1(dst + i * L.plane + (long long)y * L.pitch + x, (float)(in[k] - w[i]));
+        const double dv = in[k] - w[i];
+        Storage<T>::store1(dst + i * L.plane + (long long)y * L.pitch + x,
+                           std::is_same<T, float>::value ? (float)dv
+                                                         : (float)((dv - (double)ref_e_of(L, i)) * (double)L.ref_iq));
     }
 }
 
@@ -1278,7 +1329,8 @@ __global__ void init_kernel(T *__restrict__ dst, Lattice L, float drho, float ux
 #pragma unroll
         for (int j = 1; j < 9; ++j)
             if (i == j) v = e[j];
-        Storage<T>::store1(dst + i * L.plane + (long long)y * L.pitch + x, v);
+        Storage<T>::store1(dst + i * L.plane + (long long)y * L.pitch + x,
+                           std::is_same<T, float>::value ? v : (v - ref_e_of(L, i)) * L.ref_iq);
     }
 }
 

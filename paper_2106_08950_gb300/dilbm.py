@@ -126,6 +126,10 @@ def load_library(path: Optional[str] = None):
     L.dilbm_batch_destroy.argtypes = [vp]
     L.dilbm_batch_destroy.restype = None
     L.dilbm_batch_errors.argtypes = [vp, C.POINTER(C.c_int)]
+    L.dilbm_autotune.argtypes = [vp, ip, C.POINTER(C.c_int), C.POINTER(C.c_int)]
+    L.dilbm_set_shape.argtypes = [vp, ip, ip]
+    L.dilbm_batch_autotune.argtypes = [vp, ip, C.POINTER(C.c_int), C.POINTER(C.c_int)]
+    L.dilbm_batch_set_shape.argtypes = [vp, ip, ip]
     L.dilbm_footprint.argtypes = [C.POINTER(Grid), ip, C.POINTER(C.c_ulonglong)]
     L.dilbm_server_create.argtypes = [C.POINTER(ServerConfig), vp, C.POINTER(vp)]
     L.dilbm_server_submit.argtypes = [vp, C.POINTER(Job), C.POINTER(C.c_longlong)]
@@ -143,7 +147,8 @@ def load_library(path: Optional[str] = None):
                  "dilbm_sweep_time", "dilbm_batch_create", "dilbm_batch_step", "dilbm_batch_sync",
                  "dilbm_batch_set_timing", "dilbm_batch_sweep_time", "dilbm_batch_errors", "dilbm_footprint",
                  "dilbm_server_create", "dilbm_server_submit", "dilbm_server_progress", "dilbm_server_status",
-                 "dilbm_server_result", "dilbm_force_mean", "dilbm_force_mean_reset"):
+                 "dilbm_server_result", "dilbm_force_mean", "dilbm_force_mean_reset", "dilbm_autotune",
+                 "dilbm_set_shape", "dilbm_batch_autotune", "dilbm_batch_set_shape"):
         getattr(L, name).restype = C.c_int
     if path == LIB_PATH:
         _lib = L
@@ -306,6 +311,17 @@ class Simulation:
         """``arr``: a ctypes array of Particle (e.g. in pinned memory)."""
         check(self.L.dilbm_set_particles(self.h, arr, self.np))
 
+    # -- launch shape
+    def autotune(self, reps: int = 5):
+        """Time the candidate sweep shapes on this lattice, keep the fastest;
+        returns (warps per block, blocks per SM)."""
+        w, b = C.c_int(), C.c_int()
+        check(self.L.dilbm_autotune(self.h, int(reps), C.byref(w), C.byref(b)))
+        return w.value, b.value
+
+    def set_shape(self, warps: int, blocks_per_sm: int = 0) -> None:
+        check(self.L.dilbm_set_shape(self.h, int(warps), int(blocks_per_sm)))
+
     # -- measurement
     def set_timing(self, on: bool) -> None:
         check(self.L.dilbm_set_timing(self.h, 1 if on else 0))
@@ -353,6 +369,14 @@ class Batch:
         rc = self.L.dilbm_batch_sync(self.h, C.byref(bad))
         if rc != OK:
             raise DilbmError(rc, f"member {bad.value}: " + self.L.dilbm_last_error().decode(errors="replace"))
+
+    def autotune(self, reps: int = 5):
+        w, b = C.c_int(), C.c_int()
+        check(self.L.dilbm_batch_autotune(self.h, int(reps), C.byref(w), C.byref(b)))
+        return w.value, b.value
+
+    def set_shape(self, warps: int, blocks_per_sm: int = 0) -> None:
+        check(self.L.dilbm_batch_set_shape(self.h, int(warps), int(blocks_per_sm)))
 
     def set_timing(self, on: bool) -> None:
         check(self.L.dilbm_batch_set_timing(self.h, 1 if on else 0))
