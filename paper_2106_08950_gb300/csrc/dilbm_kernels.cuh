@@ -244,35 +244,8 @@ __device__ __forceinline__ void eq_dev9(float drho, float rho, float ux, float u
 // B = omega j + phi rho (u_s - u*): the momentum handed to the fluid is formed
 // without dividing by rho, so no rounding of j / rho biases it.  The force
 // part of M is formed from (u_s - u*) and (u_s + u*) rather than as a
-// difference of squares.
-__device__ __forceinline__ void collide(float d[9], float omega, float drho, float rho, float jx, float jy,
-                                        float ux, float uy, float kphi, float prho, float dux, float duy,
-                                        float usx, float usy, float uax, float uay) {
-    const float orho = omega * rho;
-    const float Bx = fmaf(omega, jx, prho * dux), By = fmaf(omega, jy, prho * duy);
-    const float Mxx = fmaf(orho * ux, ux, kphi * (dux * (usx + uax)));
-    const float Myy = fmaf(orho * uy, uy, kphi * (duy * (usy + uay)));
-    const float Mxy = fmaf(orho * ux, uy, kphi * fmaf(dux, usy, uax * duy));
-    float X[9];
-    moment_form(omega * drho, Bx, By, Mxx, Myy, Mxy, X);
-#pragma unroll
-    for (int i = 0; i < 9; ++i) d[i] += fmaf(-omega, d[i], X[i]);
-}
-
-// The same collision with phi = 0 (plain BGK of Eq. 1): X_i = omega d^eq_i,
-// B = omega j.
-__device__ __forceinline__ void collide_plain(float d[9], float omega, float drho, float rho, float jx, float jy,
-                                              float ux, float uy) {
-    const float orho = omega * rho;
-    const float Bx = omega * jx, By = omega * jy;
-    float X[9];
-    moment_form(omega * drho, Bx, By, orho * ux * ux, orho * uy * uy, orho * ux * uy, X);
-#pragma unroll
-    for (int i = 0; i < 9; ++i) d[i] += fmaf(-omega, d[i], X[i]);
-}
-
-// ---- the same collision on two nodes at once, with the paired FP32
-// instructions of sm_100+ (each component rounds exactly as the scalar op).
+// difference of squares.  Nodes go in pairs on the paired FP32 instructions
+// of sm_100+ (each component rounds exactly as the scalar op).
 __device__ __forceinline__ float2 f2(float a) { return make_float2(a, a); }
 __device__ __forceinline__ float2 add2(float2 a, float2 b) { return __fadd2_rn(a, b); }
 __device__ __forceinline__ float2 sub2(float2 a, float2 b) { return __fadd2_rn(a, make_float2(-b.x, -b.y)); }
@@ -295,21 +268,23 @@ __device__ __forceinline__ void moment_form2(float2 m0, float2 Bx, float2 By, fl
     X[6] = add2(am, bm); X[8] = sub2(am, bm);
 }
 
-__device__ __forceinline__ void relax2(float2 d[9], float2 omega, const float2 X[9]) {
-    const float2 nom = make_float2(-omega.x, -omega.y);
+// d + (X - omega d): the small change is rounded on its own before it is
+// added (a single fma((1 - omega), d, X) measured ~15% larger errors against
+// the FP64 oracle on wall-driven flow).
+__device__ __forceinline__ void relax2(float2 d[9], float omega, const float2 X[9]) {
 #pragma unroll
-    for (int i = 0; i < 9; ++i) d[i] = add2(d[i], fma2(nom, d[i], X[i]));
+    for (int i = 0; i < 9; ++i) d[i] = add2(d[i], fma2(f2(-omega), d[i], X[i]));
 }
 
-__device__ __forceinline__ void collide_plain2(float2 d[9], float omega, float2 drho, float2 rho, float2 jx,
-                                               float2 jy, float2 ux, float2 uy) {
+// phi = 0 (plain BGK of Eq. 1): B = omega j and, as rho u = j,
+// M = omega rho u u^T = B u^T.
+__device__ __forceinline__ void collide_plain2(float2 d[9], float omega, float2 drho, float2 jx, float2 jy,
+                                               float2 ux, float2 uy) {
     const float2 om = f2(omega);
-    const float2 orho = mul2(om, rho);
-    const float2 rux = mul2(orho, ux);
+    const float2 Bx = mul2(om, jx), By = mul2(om, jy);
     float2 X[9];
-    moment_form2(mul2(om, drho), mul2(om, jx), mul2(om, jy), mul2(rux, ux), mul2(mul2(orho, uy), uy),
-                 mul2(rux, uy), X);
-    relax2(d, om, X);
+    moment_form2(mul2(om, drho), Bx, By, mul2(Bx, ux), mul2(By, uy), mul2(Bx, uy), X);
+    relax2(d, omega, X);
 }
 
 __device__ __forceinline__ void collide2(float2 d[9], float omega, float2 drho, float2 rho, float2 jx, float2 jy,
@@ -324,7 +299,7 @@ __device__ __forceinline__ void collide2(float2 d[9], float omega, float2 drho, 
     const float2 Mxy = fma2(rux, uy, mul2(kphi, fma2(dux, usy, mul2(uax, duy))));
     float2 X[9];
     moment_form2(mul2(om, drho), Bx, By, Mxx, Myy, Mxy, X);
-    relax2(d, om, X);
+    relax2(d, omega, X);
 }
 
 // Tile ranges along one axis covered by [X - R, X + R] (a disc's bounding
@@ -629,6 +604,7 @@ __device__ __forceinline__ bool sweep_segment(const SweepArgs<T> &A, int y, int 
     int best[VEC], best_id[VEC];
 #pragma unroll
     for (int q = 0; q < VEC; ++q) { phi[q] = 0.f; rxn[q] = 0.f; ryn[q] = 0.f; best[q] = -1; best_id[q] = 0x7fffffff; }
+    // (ncand is warp-uniform; a segment no particle reaches skips all of it)
     for (int c = 0; c < ncand; ++c) {
         const float4 ra = crec[c], rb = crec[MAXC + c];
         const float R = rb.x + ph.cut;
@@ -684,9 +660,9 @@ __device__ __forceinline__ bool sweep_segment(const SweepArgs<T> &A, int y, int 
         }
     }
     // warps with no node inside any particle's phi tail collide without the force term
-    const bool coupled = __any_sync(0xffffffffu, max(max(best[0], best[1]), max(best[2], best[3])) >= 0);
+    const bool coupled = ncand > 0 && __any_sync(0xffffffffu, max(max(best[0], best[1]), max(best[2], best[3])) >= 0);
     float acc[VEC][3];
-    bool bad = false;
+    unsigned badmax = 0u;
 
     // nodes in pairs (2h, 2h + 1) on the paired FP32 instructions
 #pragma unroll
@@ -715,12 +691,17 @@ __device__ __forceinline__ bool sweep_segment(const SweepArgs<T> &A, int y, int 
         const float2 rho = add2(f2(1.0f), drho);
         const float2 jx = add2(add2(sub2(dk[1], dk[3]), sub2(dk[5], dk[6])), sub2(dk[8], dk[7]));
         const float2 jy = sub2(add2(sub2(dk[2], dk[4]), add2(dk[5], dk[6])), add2(dk[7], dk[8]));
-        const float2 inv = make_float2(1.0f / rho.x, 1.0f / rho.y);
-        const float2 ua = mul2(jx, inv), va = mul2(jy, inv);     // u* (Eq. 16)
+        // u* (Eq. 16); CUDA's correctly rounded reciprocal (a biased one would
+        // bias u* the same way on every node and step)
+        const float2 inv = make_float2(__frcp_rn(rho.x), __frcp_rn(rho.y));
+        const float2 ua = mul2(jx, inv), va = mul2(jy, inv);
         const bool act_a = x0 + qa < L.nx, act_b = x0 + qb < L.nx;
         if (MODE == MODE_STEP) {
-            if (act_a && (!(rho.x > 0.0f) || !isfinite(ua.x + va.x))) bad = true;
-            if (act_b && (!(rho.y > 0.0f) || !isfinite(ua.y + va.y))) bad = true;
+            // unstable: rho <= 0 or not finite (a non-finite population makes
+            // rho non-finite); as unsigned, bits(rho) - 1 exceeds the largest
+            // finite float's bits - 1 exactly then
+            badmax = max(badmax, act_a ? __float_as_uint(rho.x) - 1u : 0u);
+            badmax = max(badmax, act_b ? __float_as_uint(rho.y) - 1u : 0u);
         }
         acc[qa][0] = acc[qa][1] = acc[qa][2] = 0.f;
         acc[qb][0] = acc[qb][1] = acc[qb][2] = 0.f;
@@ -742,7 +723,7 @@ __device__ __forceinline__ bool sweep_segment(const SweepArgs<T> &A, int y, int 
                 }
                 continue;
             }
-            collide_plain2(dk, ph.omega, drho, rho, jx, jy, ua, va);
+            collide_plain2(dk, ph.omega, drho, jx, jy, ua, va);
         } else {
             // u_s - u* from the particle velocity carried as FP32 hi + lo:
             // u_s = U + omega x r with r the node's offset from the centre
@@ -804,7 +785,7 @@ __device__ __forceinline__ bool sweep_segment(const SweepArgs<T> &A, int y, int 
     }
 
     if (MODE == MODE_FIELDS) return true;
-    if (__any_sync(0xffffffffu, bad) && lane == 0) atomicOr(A.err, ERR_UNSTABLE);
+    if (__any_sync(0xffffffffu, badmax > 0x7f7ffffeu) && lane == 0) atomicOr(A.err, ERR_UNSTABLE);
 
     // ---- store the collided populations
     {
