@@ -3,6 +3,7 @@
 #include "dilbm.h"
 #include "dilbm_launch.cuh"
 
+#include <algorithm>
 #include <cmath>
 #include <cstdio>
 #include <cstdlib>
@@ -125,7 +126,7 @@ unsigned long long footprint_of(int nx, int ny, size_t elem, int np) {
     b += 10ull * npa * sizeof(double) + 4ull * npa * sizeof(float) + npa * sizeof(int);   // particle state
     b += 6ull * npa * sizeof(double) + 2ull * npa * sizeof(double) + sizeof(int);         // force, fsum, fcol, err
     b += ntiles * MAXC * TILE_H * sizeof(float4);                                         // partials
-    b += 2ull * (ntiles * sizeof(int) + ntiles * MAXC * sizeof(int) + ntiles * MAXC * NREC * sizeof(float4) +
+    b += 2ull * ((ntiles + 3) / 4 * 4 * sizeof(int) + ntiles * MAXC * sizeof(int) + ntiles * MAXC * NREC * sizeof(float4) +
                  npa * MAXT * sizeof(int) + npa * sizeof(int));                           // bins, two parities
     return b;
 }
@@ -209,11 +210,12 @@ SweepArgs<T> sweep_args(const dilbm_ctx *c, int cur, const void *src, void *dst,
     a.dst = (T *)dst;
     a.L = c->L;
     a.ph = c->ph;
-    a.B = c->bins[cur];
+    a.B = c->np > 0 ? c->bins[cur] : Bins{};     // no particles: no bins to read
     a.partial = c->partial;
     a.clear = (clear && c->np > 0) ? c->bins[cur ^ 1].count : nullptr;
     a.err = c->err;
     a.fo = fo;
+    a.pre = c->shape.prefetch;
     return a;
 }
 
@@ -489,7 +491,8 @@ int dilbm_create(const dilbm_grid *g, dilbm_lattice lattice, double tau, double 
         return bail(rc);
     for (int b = 0; b < 2; ++b) {
         Bins &B = c->bins[b];
-        if ((rc = dev_alloc(c, &B.count, (size_t)c->ntiles)) || (rc = dev_alloc(c, &B.ids, (size_t)c->ntiles * MAXC)) ||
+        // counts of a multiple of 4 tiles: the sweep copies them in 16-byte chunks
+        if ((rc = dev_alloc(c, &B.count, (size_t)(c->ntiles + 3) / 4 * 4)) || (rc = dev_alloc(c, &B.ids, (size_t)c->ntiles * MAXC)) ||
             (rc = dev_alloc(c, &B.rec, (size_t)c->ntiles * MAXC * NREC)) ||
             (rc = dev_alloc(c, &B.pslot, (size_t)npa * MAXT)) || (rc = dev_alloc(c, &B.npslot, (size_t)npa)))
             return bail(rc);
@@ -503,8 +506,8 @@ int dilbm_create(const dilbm_grid *g, dilbm_lattice lattice, double tau, double 
         (e = cudaMemsetAsync(c->force, 0, sizeof(double) * 3 * npa, c->stream)) != cudaSuccess ||
         (e = cudaMemsetAsync(c->fsum, 0, sizeof(double) * 3 * npa, c->stream)) != cudaSuccess ||
         (e = cudaMemsetAsync(c->fcol, 0, sizeof(double) * 2 * npa, c->stream)) != cudaSuccess ||
-        (e = cudaMemsetAsync(c->bins[0].count, 0, sizeof(int) * c->ntiles, c->stream)) != cudaSuccess ||
-        (e = cudaMemsetAsync(c->bins[1].count, 0, sizeof(int) * c->ntiles, c->stream)) != cudaSuccess)
+        (e = cudaMemsetAsync(c->bins[0].count, 0, sizeof(int) * ((c->ntiles + 3) / 4 * 4), c->stream)) != cudaSuccess ||
+        (e = cudaMemsetAsync(c->bins[1].count, 0, sizeof(int) * ((c->ntiles + 3) / 4 * 4), c->stream)) != cudaSuccess)
         return bail(cuda_fail(e, "cudaMemsetAsync"));
     // uniform initial state f^eq(rho_init, u0)
     const int blocks = 152 * 8;
@@ -774,6 +777,7 @@ void build_sweep_params(dilbm_batch *b) {
         for (int phase = 0; phase < 2; ++phase) {
             BatchArgs<T> *ba = static_cast<BatchArgs<T> *>(std::calloc(1, sizeof(BatchArgs<T>)));
             ba->n = gn;
+            ba->pre = b->shape.prefetch;
             ba->item_start[0] = ba->tile_start[0] = 0;
             for (int k = 0; k < gn; ++k) {
                 const dilbm_ctx *c = b->members[g0 + k];
@@ -1080,16 +1084,20 @@ template <typename Occ>
 int shape_candidates(Occ occupancy, std::vector<SweepShape> *out) {
     for (int w : SHAPE_WARPS) {
         int per_sm = 0;
-        cudaError_t e = occupancy(SweepShape{w, 0}, &per_sm);
+        cudaError_t e = occupancy(SweepShape{w, 0, PRE_C}, &per_sm);
         if (e != cudaSuccess) return cuda_fail(e, "sweep occupancy");
-        out->push_back(SweepShape{w, per_sm});
-        if (per_sm >= 2) out->push_back(SweepShape{w, per_sm / 2});
+        for (int pre : {PRE_C, 0}) out->push_back(SweepShape{w, 0, pre});
+        if (w == SWEEP_WARPS && per_sm >= 2) out->push_back(SweepShape{w, per_sm / 2, PRE_C});
     }
     return DILBM_OK;
 }
 
-// Time `reps` launches of each candidate (after one untimed launch) on
-// `stream`; *best receives the fastest.
+// Time every candidate in TUNE_ROUNDS interleaved rounds of `reps` launches
+// each (after one untimed launch) on `stream`; *best receives the candidate
+// with the smallest median round time (interleaving spreads clock and
+// neighbour noise over all candidates alike).
+constexpr int TUNE_ROUNDS = 3;
+
 template <typename Launch>
 int time_shapes(cudaStream_t stream, int reps, const std::vector<SweepShape> &cands, Launch launch, SweepShape *best) {
     cudaEvent_t e0 = nullptr, e1 = nullptr;
@@ -1099,25 +1107,31 @@ int time_shapes(cudaStream_t stream, int reps, const std::vector<SweepShape> &ca
         cudaEventDestroy(e0);
         return cuda_fail(e, "cudaEventCreate");
     }
-    float best_ms = 0.f;
-    int rc = DILBM_OK;
-    for (size_t k = 0; k < cands.size() && rc == DILBM_OK; ++k) {
-        float ms = 0.f;
-        e = launch(cands[k]);
-        if (e == cudaSuccess) e = cudaEventRecord(e0, stream);
-        for (int r = 0; r < reps && e == cudaSuccess; ++r) e = launch(cands[k]);
-        if (e == cudaSuccess) e = cudaEventRecord(e1, stream);
-        if (e == cudaSuccess) e = cudaEventSynchronize(e1);
-        if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
-        if (e != cudaSuccess) rc = cuda_fail(e, "autotune launch");
-        else if (k == 0 || ms < best_ms) {
-            best_ms = ms;
-            *best = cands[k];
+    std::vector<float> ms(cands.size() * TUNE_ROUNDS, 0.f);
+    for (int r = 0; r < TUNE_ROUNDS && e == cudaSuccess; ++r) {
+        for (size_t k = 0; k < cands.size() && e == cudaSuccess; ++k) {
+            e = launch(cands[k]);
+            if (e == cudaSuccess) e = cudaEventRecord(e0, stream);
+            for (int q = 0; q < reps && e == cudaSuccess; ++q) e = launch(cands[k]);
+            if (e == cudaSuccess) e = cudaEventRecord(e1, stream);
+            if (e == cudaSuccess) e = cudaEventSynchronize(e1);
+            if (e == cudaSuccess) e = cudaEventElapsedTime(&ms[k * TUNE_ROUNDS + r], e0, e1);
         }
     }
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
-    return rc;
+    if (e != cudaSuccess) return cuda_fail(e, "autotune launch");
+    float best_ms = 0.f;
+    for (size_t k = 0; k < cands.size(); ++k) {
+        float *m = &ms[k * TUNE_ROUNDS];
+        std::sort(m, m + TUNE_ROUNDS);
+        const float med = m[TUNE_ROUNDS / 2];
+        if (k == 0 || med < best_ms) {
+            best_ms = med;
+            *best = cands[k];
+        }
+    }
+    return DILBM_OK;
 }
 
 bool tuned(const std::tuple<int, int, int, long long, long long> &key, SweepShape *out) {
@@ -1133,19 +1147,25 @@ void remember(const std::tuple<int, int, int, long long, long long> &key, const 
     g_tune[key] = sh;
 }
 
-void report_shape(const SweepShape &sh, int *warps, int *blocks_per_sm) {
+void report_shape(const SweepShape &sh, int *warps, int *blocks_per_sm, int *prefetch) {
     if (warps) *warps = sh.warps;
     if (blocks_per_sm) *blocks_per_sm = sh.blocks_per_sm;
+    if (prefetch) *prefetch = sh.prefetch;
+}
+
+bool same_shape(const SweepShape &a, const SweepShape &b) {
+    return a.warps == b.warps && a.blocks_per_sm == b.blocks_per_sm && a.prefetch == b.prefetch;
 }
 
 }  // namespace
 
 extern "C" {
 
-int dilbm_set_shape(dilbm_ctx *c, int warps, int blocks_per_sm) {
-    const SweepShape sh{warps, blocks_per_sm};
-    if (!c || !shape_valid(sh)) return fail(DILBM_ERR_INVALID_ARG, "warps must be 2, 4 or 8 and blocks_per_sm >= 0");
-    if (sh.warps != c->shape.warps || sh.blocks_per_sm != c->shape.blocks_per_sm) {
+int dilbm_set_shape(dilbm_ctx *c, int warps, int blocks_per_sm, int prefetch) {
+    const SweepShape sh{warps, blocks_per_sm, prefetch};
+    if (!c || !shape_valid(sh))
+        return fail(DILBM_ERR_INVALID_ARG, "warps must be 2, 4 or 8, blocks_per_sm >= 0 and prefetch 0 or 8");
+    if (!same_shape(sh, c->shape)) {
         DILBM_CUDA(cudaStreamSynchronize(c->stream));
         drop_graphs(c);
         c->shape = sh;
@@ -1153,9 +1173,9 @@ int dilbm_set_shape(dilbm_ctx *c, int warps, int blocks_per_sm) {
     return DILBM_OK;
 }
 
-int dilbm_autotune(dilbm_ctx *c, int reps, int *warps, int *blocks_per_sm) {
+int dilbm_autotune(dilbm_ctx *c, int reps, int *warps, int *blocks_per_sm, int *prefetch) {
     if (!c) return fail(DILBM_ERR_INVALID_ARG, "NULL context");
-    if (reps <= 0) reps = 5;
+    if (reps <= 0) reps = 10;
     const auto key = std::make_tuple(0, c->storage, has_edges(c) ? 1 : 0, (long long)c->L.nx, (long long)c->L.ny);
     SweepShape best = c->shape;
     if (!tuned(key, &best)) {
@@ -1166,26 +1186,27 @@ int dilbm_autotune(dilbm_ctx *c, int reps, int *warps, int *blocks_per_sm) {
         // each launch sweeps the current state into the other buffer: what
         // the next step writes anyway
         rc = time_shapes(c->stream, reps, cands, [&](const SweepShape &sh) { return step_sweep(c, sh); }, &best);
-        c->launches += (long long)cands.size() * (reps + 1);
+        c->launches += (long long)cands.size() * (reps + 1) * TUNE_ROUNDS;
         if (rc) return rc;
         remember(key, best);
     }
-    report_shape(best, warps, blocks_per_sm);
-    return dilbm_set_shape(c, best.warps, best.blocks_per_sm);
+    report_shape(best, warps, blocks_per_sm, prefetch);
+    return dilbm_set_shape(c, best.warps, best.blocks_per_sm, best.prefetch);
 }
 
-int dilbm_batch_set_shape(dilbm_batch *b, int warps, int blocks_per_sm) {
-    const SweepShape sh{warps, blocks_per_sm};
-    if (!b || !shape_valid(sh)) return fail(DILBM_ERR_INVALID_ARG, "warps must be 2, 4 or 8 and blocks_per_sm >= 0");
-    if (sh.warps == b->shape.warps && sh.blocks_per_sm == b->shape.blocks_per_sm) return DILBM_OK;
+int dilbm_batch_set_shape(dilbm_batch *b, int warps, int blocks_per_sm, int prefetch) {
+    const SweepShape sh{warps, blocks_per_sm, prefetch};
+    if (!b || !shape_valid(sh))
+        return fail(DILBM_ERR_INVALID_ARG, "warps must be 2, 4 or 8, blocks_per_sm >= 0 and prefetch 0 or 8");
+    if (same_shape(sh, b->shape)) return DILBM_OK;
     DILBM_CUDA(cudaStreamSynchronize(b->stream));
     b->shape = sh;
     return prepare_batch(b);     // re-capture the graphs in the new shape
 }
 
-int dilbm_batch_autotune(dilbm_batch *b, int reps, int *warps, int *blocks_per_sm) {
+int dilbm_batch_autotune(dilbm_batch *b, int reps, int *warps, int *blocks_per_sm, int *prefetch) {
     if (!b) return fail(DILBM_ERR_INVALID_ARG, "NULL batch");
-    if (reps <= 0) reps = 5;
+    if (reps <= 0) reps = 10;
     long long items = 0;
     for (const dilbm_ctx *c : b->members) items += (long long)c->L.ny * c->L.ntx;
     const auto key = std::make_tuple(1, b->storage, (int)b->members.size(), items, 0LL);
@@ -1214,15 +1235,15 @@ int dilbm_batch_autotune(dilbm_batch *b, int reps, int *warps, int *blocks_per_s
             &cands);
         if (rc) return rc;
         rc = time_shapes(b->stream, reps, cands, [&](const SweepShape &sh) { return batch_sweep(b, phase, sh); }, &best);
-        b->launches += (long long)cands.size() * (reps + 1) * (long long)b->sweep_params[phase].size();
+        b->launches += (long long)cands.size() * (reps + 1) * TUNE_ROUNDS * (long long)b->sweep_params[phase].size();
         if (rc) return rc;
         remember(key, best);
         if ((e = cudaEventRecord(b->ev_out, b->stream)) != cudaSuccess) return cuda_fail(e, "cudaEventRecord");
         for (cudaStream_t s : b->member_streams)
             if ((e = cudaStreamWaitEvent(s, b->ev_out, 0)) != cudaSuccess) return cuda_fail(e, "cudaStreamWaitEvent");
     }
-    report_shape(best, warps, blocks_per_sm);
-    return dilbm_batch_set_shape(b, best.warps, best.blocks_per_sm);
+    report_shape(best, warps, blocks_per_sm, prefetch);
+    return dilbm_batch_set_shape(b, best.warps, best.blocks_per_sm, best.prefetch);
 }
 
 }  // extern "C"

@@ -112,9 +112,20 @@ template <> struct Storage<__nv_bfloat16> {
 template <typename T> __host__ __device__ constexpr int halo_of() { return 16 / (int)sizeof(T); }
 template <typename T> __host__ __device__ constexpr int segw_of() { return TILE_W + 2 * halo_of<T>(); }
 
+// A stage holds the 9 staged rows and, behind them, the segment's tile
+// header copied with them: the 16-byte chunk of tile counts that holds the
+// tile's and, when the launch asks for it (pre == PRE_C), the ids and records
+// of the tile's first PRE_C candidates.
+constexpr int PRE_C = 8;
+constexpr int HDR_IDS = 16, HDR_RECS = HDR_IDS + PRE_C * 4;
+constexpr int STAGE_EXTRA = HDR_RECS + PRE_C * NREC * 16;      // bytes, a multiple of 16
+template <typename T> __host__ __device__ constexpr int stage_elems() {
+    return 9 * segw_of<T>() + STAGE_EXTRA / (int)sizeof(T);
+}
+
 // Dynamic shared memory of one sweep block of W warps.
 template <typename T, int W = SWEEP_WARPS> __host__ __device__ constexpr size_t sweep_smem_bytes() {
-    return (size_t)W * STAGES * 9 * segw_of<T>() * sizeof(T)   // staged rows
+    return (size_t)W * STAGES * stage_elems<T>() * sizeof(T)   // staged rows + tile headers
            + (size_t)W * MAXC * NREC * sizeof(float4)           // candidate records
            + (size_t)W * MAXC * sizeof(int)                     // candidate ids
            + (size_t)W * STAGES * sizeof(uint64_t);             // mbarriers
@@ -390,15 +401,24 @@ __device__ __forceinline__ void bulk_copy_g2s(void *dst, const void *src, uint32
 // The population buffers carry GUARD readable elements before and after, so
 // the copies of edge segments stay inside the allocation.
 template <typename T>
-__device__ __forceinline__ void issue_segment(const T *__restrict__ src, const Lattice &L, int y, int tx, T *stage,
-                                              uint64_t *bar, int lane) {
+__device__ __forceinline__ void issue_segment(const T *__restrict__ src, const Lattice &L, const Bins &B, int pre,
+                                              int y, int tx, T *stage, uint64_t *bar, int lane) {
     constexpr int H = halo_of<T>(), SW = segw_of<T>();
-    if (lane == 0) mbar_expect_tx(bar, 9u * SW * sizeof(T));
+    const bool hdr = B.count != nullptr;          // lattices without particles have no bins
+    const uint32_t extra = hdr ? (pre ? (uint32_t)STAGE_EXTRA : 16u) : 0u;
+    if (lane == 0) mbar_expect_tx(bar, 9u * SW * sizeof(T) + extra);
     __syncwarp();
     if (lane < 9) {
         const int sy = wrap_or_clamp(y - cyof(lane), L.ny, L.per_y);
         const T *g = src + lane * L.plane + (long long)sy * L.pitch + (tx * TILE_W - H);
         bulk_copy_g2s(stage + lane * SW, g, SW * sizeof(T), bar);
+    } else if (hdr && lane < (pre ? 12 : 10)) {
+        // count arrays hold a multiple of 4 tiles, so the 16-byte chunk is in bounds
+        const int tile = (y / TILE_H) * L.ntx + tx;
+        unsigned char *h = reinterpret_cast<unsigned char *>(stage + 9 * SW);
+        if (lane == 9) bulk_copy_g2s(h, B.count + (tile & ~3), 16, bar);
+        else if (lane == 10) bulk_copy_g2s(h + HDR_IDS, B.ids + (long long)tile * MAXC, PRE_C * 4, bar);
+        else bulk_copy_g2s(h + HDR_RECS, B.rec + (long long)tile * MAXC * NREC, PRE_C * NREC * 16, bar);
     }
 }
 
@@ -488,6 +508,7 @@ struct SweepArgs {
     int *clear;                 // next step's bin counts to zero, or NULL
     int *err;                   // the lattice's error word
     FieldsOut fo;               // MODE_FIELDS outputs
+    int pre;                    // candidates whose records come with the stage: 0 or PRE_C
 };
 
 // A batched sweep walks one work list over many lattices, their descriptors
@@ -502,6 +523,7 @@ struct BatchArgs {
     int item_start[BATCH_LAUNCH_MAX + 1];
     int tile_start[BATCH_LAUNCH_MAX + 1];
     int n;
+    int pre;                    // as SweepArgs::pre, for every member
 };
 static_assert(sizeof(BatchArgs<float>) <= 32000, "batched sweep parameters exceed the parameter space");
 
@@ -536,8 +558,8 @@ struct Ring {
 // when there is one, then stream, collide, store and sum the segment's
 // force / torque.  Returns false if the bounded wait gave up.
 template <typename T, int MODE, bool EDGES>
-__device__ __forceinline__ bool sweep_segment(const SweepArgs<T> &A, int y, int tx, T *stage, Ring &ring, int s,
-                                              bool has_next, const SweepArgs<T> &An, int ny2, int nx2,
+__device__ __forceinline__ bool sweep_segment(const SweepArgs<T> &A, int pre, int y, int tx, T *stage, Ring &ring,
+                                              int s, bool has_next, const SweepArgs<T> &An, int ny2, int nx2,
                                               float4 *crec, int *cid, int lane) {
     constexpr int H = halo_of<T>(), SW = segw_of<T>();
     const Lattice &L = A.L;
@@ -546,22 +568,36 @@ __device__ __forceinline__ bool sweep_segment(const SweepArgs<T> &A, int y, int 
     const int tx0 = tx * TILE_W, ty0 = ty * TILE_H;
     const int x0 = tx0 + lane * VEC;
 
-    // ---- the tile's candidate particles (records written by the binning)
-    __syncwarp();
-    int ncand = A.B.count ? A.B.count[tile] : 0;
-    ncand = ncand > MAXC ? MAXC : ncand;
-    if (lane < ncand) {
-        const long long r = (long long)tile * MAXC + lane;
-#pragma unroll
-        for (int q = 0; q < NREC; ++q) crec[q * MAXC + lane] = A.B.rec[NREC * r + q];
-        cid[lane] = A.B.ids[r];
-    }
-
-    // ---- pull-stream from the staged rows: f_i(x, t+1) = f'_i(x - c_i, t)
+    // ---- wait for the staged rows and tile header
     // a warp-uniform decision: every lane leaves together if any gave up
+    __syncwarp();
     if (!__all_sync(0xffffffffu, mbar_wait_bounded(&ring.bars[s], (ring.parity >> s) & 1u))) return false;
     ring.parity ^= 1u << s;
     ring.pending &= ~(1u << s);
+
+    // ---- the tile's candidate particles (records written by the binning):
+    // the first PRE_C came with the stage, any further ones from global memory
+    int ncand = 0;
+    if (A.B.count) {
+        const unsigned char *h = reinterpret_cast<const unsigned char *>(stage + 9 * SW);
+        ncand = reinterpret_cast<const int *>(h)[tile & 3];
+        ncand = ncand > MAXC ? MAXC : ncand;
+        if (lane < ncand) {
+            if (lane < pre) {
+                const float4 *pr = reinterpret_cast<const float4 *>(h + HDR_RECS);
+#pragma unroll
+                for (int q = 0; q < NREC; ++q) crec[q * MAXC + lane] = pr[lane * NREC + q];
+                cid[lane] = reinterpret_cast<const int *>(h + HDR_IDS)[lane];
+            } else {
+                const long long r = (long long)tile * MAXC + lane;
+#pragma unroll
+                for (int q = 0; q < NREC; ++q) crec[q * MAXC + lane] = A.B.rec[NREC * r + q];
+                cid[lane] = A.B.ids[r];
+            }
+        }
+    }
+
+    // ---- pull-stream from the staged rows: f_i(x, t+1) = f'_i(x - c_i, t)
     const int c0 = H + lane * VEC;
     float d[9][VEC];
 #pragma unroll
@@ -576,7 +612,7 @@ __device__ __forceinline__ bool sweep_segment(const SweepArgs<T> &A, int y, int 
     // recycle the stage for the segment STAGES items ahead
     if (has_next) {
         fence_proxy_async_smem();
-        issue_segment<T>(An.src, An.L, ny2, nx2, stage, &ring.bars[s], lane);
+        issue_segment<T>(An.src, An.L, An.B, pre, ny2, nx2, stage, &ring.bars[s], lane);
         ring.pending |= 1u << s;
     }
     // periodic x: the row's first node pulls from column nx-1 and its
@@ -628,7 +664,7 @@ __device__ __forceinline__ bool sweep_segment(const SweepArgs<T> &A, int y, int 
             const float l = rb.x - sqrtf(d2);
             if (l < -ph.cut) continue;
             // (1 + tanh(2l/eps)) / 2 == 1 / (1 + exp(-4l/eps))
-            const float pc = 1.0f / (1.0f + expf(-ph.four_over_eps * l));
+            const float pc = __frcp_rn(1.0f + expf(-ph.four_over_eps * l));
             if (pc > phi[q] || (pc == phi[q] && pc > 0.f && id < best_id[q])) {
                 phi[q] = pc; best[q] = c; best_id[q] = id; rxn[q] = dx; ryn[q] = dy;
             }
@@ -789,18 +825,19 @@ __device__ __forceinline__ bool sweep_segment(const SweepArgs<T> &A, int y, int 
 
     // ---- store the collided populations
     {
-        const bool full = x0 + VEC <= L.nx;
+        T *base = A.dst + (long long)y * L.pitch + x0;
+        if (x0 + VEC <= L.nx) {
 #pragma unroll
-        for (int i = 0; i < 9; ++i) {
-            T *row = A.dst + i * L.plane + (long long)y * L.pitch;
-            const float4 v = to_store4<T>(L, i, make_float4(d[i][0], d[i][1], d[i][2], d[i][3]));
-            if (full) {
-                Storage<T>::store4(row + x0, v);
-            } else {
+            for (int i = 0; i < 9; ++i)
+                Storage<T>::store4(base + i * L.plane, to_store4<T>(L, i, make_float4(d[i][0], d[i][1], d[i][2], d[i][3])));
+        } else {
+#pragma unroll
+            for (int i = 0; i < 9; ++i) {
+                const float4 v = to_store4<T>(L, i, make_float4(d[i][0], d[i][1], d[i][2], d[i][3]));
                 const float vv[VEC] = {v.x, v.y, v.z, v.w};
 #pragma unroll
                 for (int q = 0; q < VEC; ++q)
-                    if (x0 + q < L.nx) Storage<T>::store1(row + x0 + q, vv[q]);
+                    if (x0 + q < L.nx) Storage<T>::store1(base + i * L.plane + q, vv[q]);
             }
         }
     }
@@ -839,10 +876,10 @@ struct SweepSmem {
     uint64_t *bars;
     __device__ __forceinline__ SweepSmem(unsigned char *raw, int warp) {
         constexpr int SW = segw_of<T>();
-        constexpr size_t STAGE_BYTES = (size_t)W * STAGES * 9 * SW * sizeof(T);
+        constexpr size_t STAGE_BYTES = (size_t)W * STAGES * stage_elems<T>() * sizeof(T);
         constexpr size_t REC_BYTES = (size_t)W * NREC * MAXC * sizeof(float4);
         constexpr size_t ID_BYTES = (size_t)W * MAXC * sizeof(int);
-        stages = reinterpret_cast<T *>(raw) + (size_t)warp * STAGES * 9 * SW;
+        stages = reinterpret_cast<T *>(raw) + (size_t)warp * STAGES * stage_elems<T>();
         crec = reinterpret_cast<float4 *>(raw + STAGE_BYTES) + (size_t)warp * NREC * MAXC;
         cid = reinterpret_cast<int *>(raw + STAGE_BYTES + REC_BYTES) + warp * MAXC;
         bars = reinterpret_cast<uint64_t *>(raw + STAGE_BYTES + REC_BYTES + ID_BYTES) + warp * STAGES;
@@ -890,7 +927,8 @@ sweep_kernel(const __grid_constant__ SweepArgs<T> one)
         int py = y, ptx = tx;
         for (int s = 0; s < STAGES; ++s) {
             if (gw + s * nw < nitems) {
-                issue_segment<T>(one.src, L, py, ptx, sm.stages + s * 9 * SW, &ring.bars[s], lane);
+                issue_segment<T>(one.src, L, one.B, one.pre, py, ptx, sm.stages + s * stage_elems<T>(), &ring.bars[s],
+                                 lane);
                 ring.pending |= 1u << s;
             }
             advance(py, ptx);
@@ -909,7 +947,7 @@ sweep_kernel(const __grid_constant__ SweepArgs<T> one)
         }
         const int s = k % STAGES;
         const bool has_next = item + STAGES * nw < nitems;
-        if (!sweep_segment<T, MODE, EDGES>(one, y, tx, sm.stages + s * 9 * SW, ring, s, has_next, one, ay, atx,
+        if (!sweep_segment<T, MODE, EDGES>(one, one.pre, y, tx, sm.stages + s * stage_elems<T>(), ring, s, has_next, one, ay, atx,
                                            sm.crec, sm.cid, lane)) {
             timed_out = true;
             break;
@@ -976,8 +1014,8 @@ sweep_batch_kernel(const __grid_constant__ BatchArgs<T> ba)
         const int it = gw + s * nw;
         if (it < nitems) {
             cursor_seek(ba, ahead, it);
-            issue_segment<T>(ba.a[ahead.lat].src, ba.a[ahead.lat].L, ahead.y, ahead.tx, sm.stages + s * 9 * SW,
-                             &ring.bars[s], lane);
+            issue_segment<T>(ba.a[ahead.lat].src, ba.a[ahead.lat].L, ba.a[ahead.lat].B, ba.pre, ahead.y, ahead.tx,
+                             sm.stages + s * stage_elems<T>(), &ring.bars[s], lane);
             ring.pending |= 1u << s;
         }
     }
@@ -993,8 +1031,8 @@ sweep_batch_kernel(const __grid_constant__ BatchArgs<T> ba)
         const bool has_next = nxt < nitems;
         if (has_next) cursor_seek(ba, ahead, nxt);
         const int nlat = has_next ? ahead.lat : cur.lat;
-        if (!sweep_segment<T, MODE, true>(ba.a[cur.lat], cur.y, cur.tx, sm.stages + s * 9 * SW, ring, s, has_next,
-                                          ba.a[nlat], ahead.y, ahead.tx, sm.crec, sm.cid, lane)) {
+        if (!sweep_segment<T, MODE, true>(ba.a[cur.lat], ba.pre, cur.y, cur.tx, sm.stages + s * stage_elems<T>(), ring,
+                                          s, has_next, ba.a[nlat], ahead.y, ahead.tx, sm.crec, sm.cid, lane)) {
             timed_out = true;
             break;
         }
