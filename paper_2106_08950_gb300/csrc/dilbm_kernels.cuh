@@ -608,6 +608,37 @@ __device__ __forceinline__ bool sweep_segment(const SweepArgs<T> &A, int pre, in
         v = from_store4<T>(L, i, v);
         d[i][0] = v.x; d[i][1] = v.y; d[i][2] = v.z; d[i][3] = v.w;
     }
+    const bool row_edge = EDGES && !L.per_y && (y == 0 || y == L.ny - 1);
+    const bool col_edge = EDGES && !L.per_x && (tx == 0 || tx0 + TILE_W >= L.nx);
+    // west / east edge nodes of a row that is not itself an edge row take
+    // the inner neighbour's (x + 1 or x - 1, same row) streamed values: from
+    // this thread's registers, from the left lane's, or -- for an east edge
+    // that opens its segment (nx = 1 mod 128) -- pulled from the staged halo,
+    // which is why this runs before the stage is recycled
+    if (col_edge && !row_edge) {
+        float left[9];
+#pragma unroll
+        for (int i = 0; i < 9; ++i) left[i] = __shfl_up_sync(0xffffffffu, d[i][VEC - 1], 1);
+        if (lane == 0 && x0 == L.nx - 1) {
+#pragma unroll
+            for (int i = 0; i < 9; ++i)
+                left[i] = from_store<T>(L, i, Storage<T>::lds1(stage + i * SW + (c0 - 1 - cxof(i))));
+        }
+#pragma unroll
+        for (int q = 0; q < VEC; ++q) {
+            const int x = x0 + q;
+            if (x != 0 && x != L.nx - 1) continue;
+            float dn[9], e[9];
+#pragma unroll
+            for (int i = 0; i < 9; ++i) {
+                if (x == 0) dn[i] = d[i][q < VEC - 1 ? q + 1 : q];            // q == 0 here: x0 == 0
+                else dn[i] = q > 0 ? d[i][q > 0 ? q - 1 : 0] : left[i];
+            }
+            extrapolate(L, x == 0 ? WEST : EAST, dn, e);
+#pragma unroll
+            for (int i = 0; i < 9; ++i) d[i][q] = e[i];
+        }
+    }
     __syncwarp();
     // recycle the stage for the segment STAGES items ahead
     if (has_next) {
@@ -671,30 +702,6 @@ __device__ __forceinline__ bool sweep_segment(const SweepArgs<T> &A, int pre, in
         }
     }
 
-    const bool row_edge = EDGES && !L.per_y && (y == 0 || y == L.ny - 1);
-    const bool col_edge = EDGES && !L.per_x && (tx == 0 || tx0 + TILE_W >= L.nx);
-    // west / east edge nodes of a row that is not itself an edge row: the
-    // inner neighbour (x + 1 or x - 1, same row) is in this thread's registers
-    // or, for the east edge at the start of a chunk, in the left lane's
-    if (col_edge && !row_edge) {
-        float left[9];
-#pragma unroll
-        for (int i = 0; i < 9; ++i) left[i] = __shfl_up_sync(0xffffffffu, d[i][VEC - 1], 1);
-#pragma unroll
-        for (int q = 0; q < VEC; ++q) {
-            const int x = x0 + q;
-            if (x != 0 && x != L.nx - 1) continue;
-            float dn[9], e[9];
-#pragma unroll
-            for (int i = 0; i < 9; ++i) {
-                if (x == 0) dn[i] = d[i][q < VEC - 1 ? q + 1 : q];            // q == 0 here: x0 == 0
-                else dn[i] = q > 0 ? d[i][q > 0 ? q - 1 : 0] : left[i];
-            }
-            extrapolate(L, x == 0 ? WEST : EAST, dn, e);
-#pragma unroll
-            for (int i = 0; i < 9; ++i) d[i][q] = e[i];
-        }
-    }
     // warps with no node inside any particle's phi tail collide without the force term
     const bool coupled = ncand > 0 && __any_sync(0xffffffffu, max(max(best[0], best[1]), max(best[2], best[3])) >= 0);
     float acc[VEC][3];

@@ -25,7 +25,8 @@ def mixed_problems():
     probs = [W.cylinder_drag(nx=150, ny=60, r=8.0, cx=40.0, cy=30.0),
              W.sedimentation(nx=70, ny=130, r=6.0, rho_s=1.5, g=2e-5, y0=80.0),
              W.periodic_suspension(n=200, count=6, seed=5, rmin=4, rmax=8),
-             W.Problem(nx=37, ny=23, tau=0.8, eps=2.0, u0=(0.01, 0.0))]          # no particles, ragged
+             W.Problem(nx=37, ny=23, tau=0.8, eps=2.0, u0=(0.01, 0.0)),          # no particles, ragged
+             W.cylinder_drag(nx=129, ny=45, r=7.0, cx=50.0, cy=22.0)]            # east edge alone in its segment
     probs += [W.random_job(rng, nx_range=(64, 300), ny_range=(64, 300), p_range=(1, 8)) for _ in range(4)]
     return probs
 

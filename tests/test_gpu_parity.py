@@ -68,6 +68,23 @@ def test_periodic_moving_particles(stream):
     assert_parity(g, o, force_tol=PAR.TOL_FP32_SUSPENSION_FORCE)
 
 
+@pytest.mark.parametrize("nx", [129, 257])
+def test_east_edge_opening_a_row_segment(stream, nx):
+    # nx = 1 (mod 128): the east edge node is alone in the last row segment and
+    # its inner neighbour lies in the previous segment.  Inlet / outlet channel,
+    # periodic in y with a ragged last tile row (ny = 37).
+    prob = W.cylinder_drag(nx=nx, ny=37, r=6.0, cx=40.0, cy=18.3, re=15.0)
+    g, o = run_both(prob, 300, stream)
+    assert_parity(g, o)
+
+
+def test_east_wall_opening_a_row_segment(stream):
+    # the same geometry against a no-slip east wall, in a closed box
+    prob = W.sedimentation(nx=129, ny=70, r=6.0, rho_s=1.5, g=2e-5, x0=121.0, y0=40.0)
+    g, o = run_both(prob, 300, stream)
+    assert_parity(g, o, force_tol=PAR.TOL_FP32_SUSPENSION_FORCE)
+
+
 def test_ragged_lattice_not_multiple_of_four(stream):
     prob = moving_particles(nx=130, ny=21)
     prob.particles = [W.Particle(128.4, 10.3, 4.0, ux=0.01, omega=0.003, rho_s=1.2),
