@@ -672,11 +672,15 @@ __device__ __forceinline__ bool sweep_segment(const SweepArgs<T> &A, int pre, in
 #pragma unroll
     for (int q = 0; q < VEC; ++q) { phi[q] = 0.f; rxn[q] = 0.f; ryn[q] = 0.f; best[q] = -1; best_id[q] = 0x7fffffff; }
     // (ncand is warp-uniform; a segment no particle reaches skips all of it)
+    const float inv_nx = 1.0f / (float)L.nx, inv_ny = 1.0f / (float)L.ny;
     for (int c = 0; c < ncand; ++c) {
         const float4 ra = crec[c], rb = crec[MAXC + c];
         const float R = rb.x + ph.cut;
         float dy = ((float)(y - ty0) - ra.z) - ra.w;
-        if (L.wrap_y) { if (dy >= 0.5f * L.ny) dy -= L.ny; else if (dy < -0.5f * L.ny) dy += L.ny; }
+        // short periodic axes: the stored image may lie several periods away
+        // (it is the one nearest the tile centre), so reduce by the nearest
+        // multiple of the period (exact: an integer multiple of an integer)
+        if (L.wrap_y) dy = fmaf(-(float)L.ny, rintf(dy * inv_ny), dy);
         const float h2 = R * R - dy * dy;
         if (h2 < 0.f) continue;                         // this row misses the disc tail
         const float dx0 = ((float)(x0 - tx0) - ra.x) - ra.y;
@@ -689,7 +693,7 @@ __device__ __forceinline__ bool sweep_segment(const SweepArgs<T> &A, int pre, in
 #pragma unroll
         for (int q = 0; q < VEC; ++q) {
             float dx = dx0 + (float)q;
-            if (L.wrap_x) { if (dx >= 0.5f * L.nx) dx -= L.nx; else if (dx < -0.5f * L.nx) dx += L.nx; }
+            if (L.wrap_x) dx = fmaf(-(float)L.nx, rintf(dx * inv_nx), dx);
             const float d2 = dx * dx + dy * dy;
             if (d2 > R * R) continue;
             const float l = rb.x - sqrtf(d2);

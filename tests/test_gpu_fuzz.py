@@ -1,0 +1,86 @@
+"""Seeded sweep of small lattices against the FP64 oracle.
+
+Sizes are drawn so that every residue the sweep treats specially comes up:
+nx = 1, 2, 127, 0 (mod 128) (an edge alone in, or ending, a row segment),
+every nx mod 4 (ragged thread chunks), every ny mod 8 (ragged tile rows), and
+the smallest lattices.  Sides are periodic, velocity (walls, inlets) or
+pressure (outlets) in every combination the boundary rules allow; 0-4 discs,
+fixed or free.  Each case runs through the C ABI and is compared node by node
+and particle by particle with the FP32 tolerances.
+"""
+import numpy as np
+import pytest
+
+from oracle import oracle as O
+from paper_2106_08950_gb300 import dilbm as D
+from paper_2106_08950_gb300 import workloads as W
+from tests import parity as PAR
+
+pytestmark = pytest.mark.gpu
+
+NX = [3, 4, 5, 6, 7, 31, 33, 127, 128, 129, 130, 131, 255, 257, 385]
+NY = [3, 5, 7, 8, 9, 15, 16, 17, 24, 33, 47, 64, 71]
+
+
+@pytest.fixture(scope="module")
+def stream():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    D.load_library()
+    return int(torch.cuda.Stream().cuda_stream)
+
+
+def side(rng, kind):
+    if kind == "velocity":
+        return W.Side(W.VELOCITY, float(rng.uniform(-0.02, 0.03)), float(rng.uniform(-0.01, 0.01)), 1.0)
+    return W.Side(W.PRESSURE, 0.0, 0.0, float(rng.uniform(0.995, 1.005)))
+
+
+def random_case(seed):
+    rng = np.random.default_rng(1000 + seed)
+    nx, ny = int(rng.choice(NX)), int(rng.choice(NY))
+    per_x, per_y = bool(rng.random() < 0.4), bool(rng.random() < 0.4)
+    kinds = ["velocity", "pressure"]
+    west = W.Side() if per_x else side(rng, str(rng.choice(kinds)))
+    east = W.Side() if per_x else side(rng, str(rng.choice(kinds)))
+    south = W.Side() if per_y else side(rng, "velocity")
+    north = W.Side() if per_y else side(rng, str(rng.choice(kinds)))
+    parts = []
+    room = min(nx, ny)
+    if room >= 14:
+        for _ in range(int(rng.integers(0, 5))):
+            r = float(rng.uniform(2.5, min(8.0, room / 4)))
+            x = float(rng.uniform(r + 1, nx - r - 2)) if not per_x else float(rng.uniform(0, nx))
+            y = float(rng.uniform(r + 1, ny - r - 2)) if not per_y else float(rng.uniform(0, ny))
+            if all((x - q.x) ** 2 + (y - q.y) ** 2 > (r + q.r + 4) ** 2 for q in parts):
+                parts.append(W.Particle(x, y, r, ux=float(rng.uniform(-0.01, 0.01)),
+                                        uy=float(rng.uniform(-0.01, 0.01)), omega=float(rng.uniform(-1e-3, 1e-3)),
+                                        rho_s=float(rng.uniform(1.1, 1.6)), fixed=bool(rng.random() < 0.3)))
+    tau = float(rng.uniform(0.6, 1.2))
+    u0 = (float(rng.uniform(-0.01, 0.02)), float(rng.uniform(-0.01, 0.01)))
+    prob = W.Problem(nx=nx, ny=ny, tau=tau, eps=float(rng.uniform(1.5, 2.5)), west=west, east=east,
+                     south=south, north=north, u0=u0, gravity=(0.0, -1e-5),
+                     wan_turek=W.wan_turek_defaults(4.0, 1.3, 1.0, 1e-5), particles=parts,
+                     name=f"fuzz {seed}: {nx}x{ny}")
+    return prob, int(rng.integers(40, 160))
+
+
+@pytest.mark.parametrize("seed", range(40))
+def test_random_lattice_matches_oracle(stream, seed):
+    prob, steps = random_case(seed)
+    g = D.Simulation(prob, stream=stream)
+    o = O.OracleSim(prob)
+    g.step(steps)
+    o.step(steps)
+    g.sync()
+    ok, errs = PAR.compare_fields(g.fields(), o.fields())
+    assert ok, (prob.name, prob.west.kind, prob.east.kind, prob.south.kind, prob.north.kind, errs)
+    if prob.particles:
+        Fg, _, Sg = g.forces()
+        Fo, _, So = o.forces()
+        ok, e = PAR.compare_forces(Fg, Fo, PAR.TOL_FP32_SUSPENSION_FORCE, max(q.r for q in prob.particles))
+        assert ok, (prob.name, e)
+        ok, e = PAR.compare_state(Sg, So)
+        assert ok, (prob.name, e)
+    g.close()

@@ -85,6 +85,20 @@ def test_east_wall_opening_a_row_segment(stream):
     assert_parity(g, o, force_tol=PAR.TOL_FP32_SUSPENSION_FORCE)
 
 
+@pytest.mark.parametrize("nx,ny", [(33, 64), (47, 22), (160, 21)])
+def test_short_periodic_axes(stream, nx, ny):
+    # Periodic axes shorter than a tile plus the disc's reach: every node takes
+    # its own minimum image of the disc, which the bins store as the image
+    # nearest the tile centre, up to several periods away.  The tail of the
+    # first disc wraps across x = 0.
+    prob = W.Problem(nx=nx, ny=ny, tau=0.85, eps=2.4, u0=(0.012, -0.008), gravity=(0.0, -1e-5),
+                     wan_turek=W.wan_turek_defaults(5.0, 1.5, 1.0, 1e-5),
+                     particles=[W.Particle(nx - 9.0, ny / 2.0 + 0.4, 6.6, ux=-0.001, uy=-0.009, rho_s=1.57),
+                                W.Particle(8.3, 2.9, 3.1, ux=0.004, uy=0.002, rho_s=1.3)])
+    g, o = run_both(prob, 150, stream)
+    assert_parity(g, o, force_tol=PAR.TOL_FP32_SUSPENSION_FORCE)
+
+
 def test_ragged_lattice_not_multiple_of_four(stream):
     prob = moving_particles(nx=130, ny=21)
     prob.particles = [W.Particle(128.4, 10.3, 4.0, ux=0.01, omega=0.003, rho_s=1.2),
