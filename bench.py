@@ -54,7 +54,7 @@ def parse():
     ap.add_argument("--max-jobs", type=int, default=64, help="serve: jobs resident at once")
     ap.add_argument("--macro-steps", type=int, default=64, help="serve: steps per macro-step")
     ap.add_argument("--shape", default=None,
-                    help="sweep launch shape warps,blocks_per_sm,prefetch (default: the autotuner's)")
+                    help="sweep launch shape warps,blocks_per_sm (default: the autotuner's)")
     return ap.parse_args()
 
 
@@ -335,7 +335,7 @@ def gpu_arm(args):
             "dtype": {"fp32": "f32", "fp16": "f16-storage/f32-math", "bf16": "bf16-storage/f32-math"}[args.storage],
             "data": "synthetic",
             "config": dict(cfg, storage=args.storage, nodes=nodes, particles=npart,
-                           launch_shape={"warps_per_block": shape[0], "blocks_per_sm": shape[1], "prefetch": shape[2],
+                           launch_shape={"warps_per_block": shape[0], "blocks_per_sm": shape[1],
                                          "by": "--shape" if args.shape else "autotuner"},
                            l2="populations 9x2 planes exceed L2; no flush",
                            parallelism=f"replicas x{world}" if world > 1 else "single GPU"),
@@ -432,8 +432,8 @@ def batch_arm(args):
                        "storage": args.storage, "nodes": nodes, "lattices": len(jobs),
                        "particles": sum(len(j.particles) for j in jobs),
                        "launch": "one batched sweep + one batched particle launch per step, CUDA-graph replay",
-                       "launch_shape": {"warps_per_block": shape[0], "blocks_per_sm": shape[1], "prefetch": shape[2],
-                                        "by": "autotuner"},
+                       "launch_shape": {"warps_per_block": shape[0], "blocks_per_sm": shape[1],
+                                        "by": "--shape" if args.shape else "autotuner"},
                        "l2": f"{nodes * BYTES_PER_NODE[args.storage] / 1e6:.0f} MB of populations per step"},
             "one_at_a_time": {"value": alone_value, "unit": "MLUPS", "steps": k_alone,
                               "speedup_of_batch": value / alone_value},

@@ -212,35 +212,33 @@ int dilbm_batch_set_timing(dilbm_batch *batch, int enable);
 int dilbm_batch_sweep_time(dilbm_batch *batch, double *ms_total, long long *launches);
 long long dilbm_batch_launch_count(const dilbm_batch *batch);
 void dilbm_batch_destroy(dilbm_batch *batch);
-int dilbm_batch_autotune(dilbm_batch *batch, int reps, int *warps, int *blocks_per_sm, int *prefetch);
-int dilbm_batch_set_shape(dilbm_batch *batch, int warps, int blocks_per_sm, int prefetch);
+int dilbm_batch_autotune(dilbm_batch *batch, int reps, int *warps, int *blocks_per_sm);
+int dilbm_batch_set_shape(dilbm_batch *batch, int warps, int blocks_per_sm);
 
 /*
  * Launch shape of the lattice sweep, and its autotuner.  A shape is the
  * number of row segments (128 nodes of one row) a block keeps in flight --
- * warps per block, 2, 4 or 8 -- the persistent blocks per SM (blocks_per_sm,
- * 0: as many as fit) and how much of a segment's tile header travels with
- * its staged rows (prefetch: 8, the tile's candidate count and its first 8
- * candidates' records; 0, the count alone, the records then read when the
- * tile has candidates).  The tile a row segment belongs to (128 x 8 nodes) is
+ * warps per block, 2, 4 or 8 -- and the persistent blocks per SM
+ * (blocks_per_sm, 0: as many as fit).  The tile a row segment belongs to
+ * (128 x 8 nodes) is
  * fixed: it orders the force partials.  Every shape runs the same arithmetic
  * on every node, so results are bit for bit the same in every shape.
  *
  * dilbm_autotune / dilbm_batch_autotune time every candidate shape (each
- * warps-per-block value with as many blocks per SM as fit and both prefetch
- * depths, and 8 warps with half the blocks) in 3 interleaved rounds of reps
+ * warps-per-block value with as many blocks per SM as fit and with half as
+ * many) in 3 interleaved rounds of reps
  * sweep launches of the current state
  * (reps <= 0: 10; the launches only write what the next step overwrites),
- * keep the one with the smallest median round time and report it in *warps,
- * *blocks_per_sm and *prefetch (nullable).  The choice is cached
+ * keep the one with the smallest median round time and report it in *warps
+ * and *blocks_per_sm (nullable).  The choice is cached
  * per process, keyed by storage, edge handling and lattice size (for a
  * batch: storage, member count and total row segments), so tuning a second
  * context or batch of the same key launches nothing.  Both synchronise.
  * dilbm_set_shape / dilbm_batch_set_shape set a shape by hand.
  * Errors: INVALID_ARG, CUDA.
  */
-int dilbm_autotune(dilbm_ctx *ctx, int reps, int *warps, int *blocks_per_sm, int *prefetch);
-int dilbm_set_shape(dilbm_ctx *ctx, int warps, int blocks_per_sm, int prefetch);
+int dilbm_autotune(dilbm_ctx *ctx, int reps, int *warps, int *blocks_per_sm);
+int dilbm_set_shape(dilbm_ctx *ctx, int warps, int blocks_per_sm);
 
 /*
  * Device memory dilbm_create allocates for a lattice of grid->nx x grid->ny

@@ -126,7 +126,7 @@ unsigned long long footprint_of(int nx, int ny, size_t elem, int np) {
     b += 10ull * npa * sizeof(double) + 4ull * npa * sizeof(float) + npa * sizeof(int);   // particle state
     b += 6ull * npa * sizeof(double) + 2ull * npa * sizeof(double) + sizeof(int);         // force, fsum, fcol, err
     b += ntiles * MAXC * TILE_H * sizeof(float4);                                         // partials
-    b += 2ull * ((ntiles + 3) / 4 * 4 * sizeof(int) + ntiles * MAXC * sizeof(int) + ntiles * MAXC * NREC * sizeof(float4) +
+    b += 2ull * (ntiles * sizeof(int) + ntiles * MAXC * sizeof(int) + ntiles * MAXC * NREC * sizeof(float4) +
                  npa * MAXT * sizeof(int) + npa * sizeof(int));                           // bins, two parities
     return b;
 }
@@ -215,7 +215,6 @@ SweepArgs<T> sweep_args(const dilbm_ctx *c, int cur, const void *src, void *dst,
     a.clear = (clear && c->np > 0) ? c->bins[cur ^ 1].count : nullptr;
     a.err = c->err;
     a.fo = fo;
-    a.pre = c->shape.prefetch;
     return a;
 }
 
@@ -491,8 +490,7 @@ int dilbm_create(const dilbm_grid *g, dilbm_lattice lattice, double tau, double 
         return bail(rc);
     for (int b = 0; b < 2; ++b) {
         Bins &B = c->bins[b];
-        // counts of a multiple of 4 tiles: the sweep copies them in 16-byte chunks
-        if ((rc = dev_alloc(c, &B.count, (size_t)(c->ntiles + 3) / 4 * 4)) || (rc = dev_alloc(c, &B.ids, (size_t)c->ntiles * MAXC)) ||
+        if ((rc = dev_alloc(c, &B.count, (size_t)c->ntiles)) || (rc = dev_alloc(c, &B.ids, (size_t)c->ntiles * MAXC)) ||
             (rc = dev_alloc(c, &B.rec, (size_t)c->ntiles * MAXC * NREC)) ||
             (rc = dev_alloc(c, &B.pslot, (size_t)npa * MAXT)) || (rc = dev_alloc(c, &B.npslot, (size_t)npa)))
             return bail(rc);
@@ -506,8 +504,8 @@ int dilbm_create(const dilbm_grid *g, dilbm_lattice lattice, double tau, double 
         (e = cudaMemsetAsync(c->force, 0, sizeof(double) * 3 * npa, c->stream)) != cudaSuccess ||
         (e = cudaMemsetAsync(c->fsum, 0, sizeof(double) * 3 * npa, c->stream)) != cudaSuccess ||
         (e = cudaMemsetAsync(c->fcol, 0, sizeof(double) * 2 * npa, c->stream)) != cudaSuccess ||
-        (e = cudaMemsetAsync(c->bins[0].count, 0, sizeof(int) * ((c->ntiles + 3) / 4 * 4), c->stream)) != cudaSuccess ||
-        (e = cudaMemsetAsync(c->bins[1].count, 0, sizeof(int) * ((c->ntiles + 3) / 4 * 4), c->stream)) != cudaSuccess)
+        (e = cudaMemsetAsync(c->bins[0].count, 0, sizeof(int) * c->ntiles, c->stream)) != cudaSuccess ||
+        (e = cudaMemsetAsync(c->bins[1].count, 0, sizeof(int) * c->ntiles, c->stream)) != cudaSuccess)
         return bail(cuda_fail(e, "cudaMemsetAsync"));
     // uniform initial state f^eq(rho_init, u0)
     const int blocks = 152 * 8;
@@ -777,7 +775,6 @@ void build_sweep_params(dilbm_batch *b) {
         for (int phase = 0; phase < 2; ++phase) {
             BatchArgs<T> *ba = static_cast<BatchArgs<T> *>(std::calloc(1, sizeof(BatchArgs<T>)));
             ba->n = gn;
-            ba->pre = b->shape.prefetch;
             ba->item_start[0] = ba->tile_start[0] = 0;
             for (int k = 0; k < gn; ++k) {
                 const dilbm_ctx *c = b->members[g0 + k];
@@ -1084,10 +1081,10 @@ template <typename Occ>
 int shape_candidates(Occ occupancy, std::vector<SweepShape> *out) {
     for (int w : SHAPE_WARPS) {
         int per_sm = 0;
-        cudaError_t e = occupancy(SweepShape{w, 0, PRE_C}, &per_sm);
+        cudaError_t e = occupancy(SweepShape{w, 0}, &per_sm);
         if (e != cudaSuccess) return cuda_fail(e, "sweep occupancy");
-        for (int pre : {PRE_C, 0}) out->push_back(SweepShape{w, 0, pre});
-        if (w == SWEEP_WARPS && per_sm >= 2) out->push_back(SweepShape{w, per_sm / 2, PRE_C});
+        out->push_back(SweepShape{w, 0});
+        if (per_sm >= 2) out->push_back(SweepShape{w, per_sm / 2});
     }
     return DILBM_OK;
 }
@@ -1147,24 +1144,22 @@ void remember(const std::tuple<int, int, int, long long, long long> &key, const 
     g_tune[key] = sh;
 }
 
-void report_shape(const SweepShape &sh, int *warps, int *blocks_per_sm, int *prefetch) {
+void report_shape(const SweepShape &sh, int *warps, int *blocks_per_sm) {
     if (warps) *warps = sh.warps;
     if (blocks_per_sm) *blocks_per_sm = sh.blocks_per_sm;
-    if (prefetch) *prefetch = sh.prefetch;
 }
 
 bool same_shape(const SweepShape &a, const SweepShape &b) {
-    return a.warps == b.warps && a.blocks_per_sm == b.blocks_per_sm && a.prefetch == b.prefetch;
+    return a.warps == b.warps && a.blocks_per_sm == b.blocks_per_sm;
 }
 
 }  // namespace
 
 extern "C" {
 
-int dilbm_set_shape(dilbm_ctx *c, int warps, int blocks_per_sm, int prefetch) {
-    const SweepShape sh{warps, blocks_per_sm, prefetch};
-    if (!c || !shape_valid(sh))
-        return fail(DILBM_ERR_INVALID_ARG, "warps must be 2, 4 or 8, blocks_per_sm >= 0 and prefetch 0 or 8");
+int dilbm_set_shape(dilbm_ctx *c, int warps, int blocks_per_sm) {
+    const SweepShape sh{warps, blocks_per_sm};
+    if (!c || !shape_valid(sh)) return fail(DILBM_ERR_INVALID_ARG, "warps must be 2, 4 or 8 and blocks_per_sm >= 0");
     if (!same_shape(sh, c->shape)) {
         DILBM_CUDA(cudaStreamSynchronize(c->stream));
         drop_graphs(c);
@@ -1173,7 +1168,7 @@ int dilbm_set_shape(dilbm_ctx *c, int warps, int blocks_per_sm, int prefetch) {
     return DILBM_OK;
 }
 
-int dilbm_autotune(dilbm_ctx *c, int reps, int *warps, int *blocks_per_sm, int *prefetch) {
+int dilbm_autotune(dilbm_ctx *c, int reps, int *warps, int *blocks_per_sm) {
     if (!c) return fail(DILBM_ERR_INVALID_ARG, "NULL context");
     if (reps <= 0) reps = 10;
     const auto key = std::make_tuple(0, c->storage, has_edges(c) ? 1 : 0, (long long)c->L.nx, (long long)c->L.ny);
@@ -1190,21 +1185,20 @@ int dilbm_autotune(dilbm_ctx *c, int reps, int *warps, int *blocks_per_sm, int *
         if (rc) return rc;
         remember(key, best);
     }
-    report_shape(best, warps, blocks_per_sm, prefetch);
-    return dilbm_set_shape(c, best.warps, best.blocks_per_sm, best.prefetch);
+    report_shape(best, warps, blocks_per_sm);
+    return dilbm_set_shape(c, best.warps, best.blocks_per_sm);
 }
 
-int dilbm_batch_set_shape(dilbm_batch *b, int warps, int blocks_per_sm, int prefetch) {
-    const SweepShape sh{warps, blocks_per_sm, prefetch};
-    if (!b || !shape_valid(sh))
-        return fail(DILBM_ERR_INVALID_ARG, "warps must be 2, 4 or 8, blocks_per_sm >= 0 and prefetch 0 or 8");
+int dilbm_batch_set_shape(dilbm_batch *b, int warps, int blocks_per_sm) {
+    const SweepShape sh{warps, blocks_per_sm};
+    if (!b || !shape_valid(sh)) return fail(DILBM_ERR_INVALID_ARG, "warps must be 2, 4 or 8 and blocks_per_sm >= 0");
     if (same_shape(sh, b->shape)) return DILBM_OK;
     DILBM_CUDA(cudaStreamSynchronize(b->stream));
     b->shape = sh;
     return prepare_batch(b);     // re-capture the graphs in the new shape
 }
 
-int dilbm_batch_autotune(dilbm_batch *b, int reps, int *warps, int *blocks_per_sm, int *prefetch) {
+int dilbm_batch_autotune(dilbm_batch *b, int reps, int *warps, int *blocks_per_sm) {
     if (!b) return fail(DILBM_ERR_INVALID_ARG, "NULL batch");
     if (reps <= 0) reps = 10;
     long long items = 0;
@@ -1242,8 +1236,8 @@ int dilbm_batch_autotune(dilbm_batch *b, int reps, int *warps, int *blocks_per_s
         for (cudaStream_t s : b->member_streams)
             if ((e = cudaStreamWaitEvent(s, b->ev_out, 0)) != cudaSuccess) return cuda_fail(e, "cudaStreamWaitEvent");
     }
-    report_shape(best, warps, blocks_per_sm, prefetch);
-    return dilbm_batch_set_shape(b, best.warps, best.blocks_per_sm, best.prefetch);
+    report_shape(best, warps, blocks_per_sm);
+    return dilbm_batch_set_shape(b, best.warps, best.blocks_per_sm);
 }
 
 }  // extern "C"

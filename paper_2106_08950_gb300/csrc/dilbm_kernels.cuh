@@ -112,20 +112,12 @@ template <> struct Storage<__nv_bfloat16> {
 template <typename T> __host__ __device__ constexpr int halo_of() { return 16 / (int)sizeof(T); }
 template <typename T> __host__ __device__ constexpr int segw_of() { return TILE_W + 2 * halo_of<T>(); }
 
-// A stage holds the 9 staged rows and, behind them, the segment's tile
-// header copied with them: the 16-byte chunk of tile counts that holds the
-// tile's and, when the launch asks for it (pre == PRE_C), the ids and records
-// of the tile's first PRE_C candidates.
-constexpr int PRE_C = 8;
-constexpr int HDR_IDS = 16, HDR_RECS = HDR_IDS + PRE_C * 4;
-constexpr int STAGE_EXTRA = HDR_RECS + PRE_C * NREC * 16;      // bytes, a multiple of 16
-template <typename T> __host__ __device__ constexpr int stage_elems() {
-    return 9 * segw_of<T>() + STAGE_EXTRA / (int)sizeof(T);
-}
+// Elements of one stage: the 9 staged rows.
+template <typename T> __host__ __device__ constexpr int stage_elems() { return 9 * segw_of<T>(); }
 
 // Dynamic shared memory of one sweep block of W warps.
 template <typename T, int W = SWEEP_WARPS> __host__ __device__ constexpr size_t sweep_smem_bytes() {
-    return (size_t)W * STAGES * stage_elems<T>() * sizeof(T)   // staged rows + tile headers
+    return (size_t)W * STAGES * stage_elems<T>() * sizeof(T)   // staged rows
            + (size_t)W * MAXC * NREC * sizeof(float4)           // candidate records
            + (size_t)W * MAXC * sizeof(int)                     // candidate ids
            + (size_t)W * STAGES * sizeof(uint64_t);             // mbarriers
@@ -401,24 +393,15 @@ __device__ __forceinline__ void bulk_copy_g2s(void *dst, const void *src, uint32
 // The population buffers carry GUARD readable elements before and after, so
 // the copies of edge segments stay inside the allocation.
 template <typename T>
-__device__ __forceinline__ void issue_segment(const T *__restrict__ src, const Lattice &L, const Bins &B, int pre,
-                                              int y, int tx, T *stage, uint64_t *bar, int lane) {
+__device__ __forceinline__ void issue_segment(const T *__restrict__ src, const Lattice &L, int y, int tx, T *stage,
+                                              uint64_t *bar, int lane) {
     constexpr int H = halo_of<T>(), SW = segw_of<T>();
-    const bool hdr = B.count != nullptr;          // lattices without particles have no bins
-    const uint32_t extra = hdr ? (pre ? (uint32_t)STAGE_EXTRA : 16u) : 0u;
-    if (lane == 0) mbar_expect_tx(bar, 9u * SW * sizeof(T) + extra);
+    if (lane == 0) mbar_expect_tx(bar, 9u * SW * sizeof(T));
     __syncwarp();
     if (lane < 9) {
         const int sy = wrap_or_clamp(y - cyof(lane), L.ny, L.per_y);
         const T *g = src + lane * L.plane + (long long)sy * L.pitch + (tx * TILE_W - H);
         bulk_copy_g2s(stage + lane * SW, g, SW * sizeof(T), bar);
-    } else if (hdr && lane < (pre ? 12 : 10)) {
-        // count arrays hold a multiple of 4 tiles, so the 16-byte chunk is in bounds
-        const int tile = (y / TILE_H) * L.ntx + tx;
-        unsigned char *h = reinterpret_cast<unsigned char *>(stage + 9 * SW);
-        if (lane == 9) bulk_copy_g2s(h, B.count + (tile & ~3), 16, bar);
-        else if (lane == 10) bulk_copy_g2s(h + HDR_IDS, B.ids + (long long)tile * MAXC, PRE_C * 4, bar);
-        else bulk_copy_g2s(h + HDR_RECS, B.rec + (long long)tile * MAXC * NREC, PRE_C * NREC * 16, bar);
     }
 }
 
@@ -508,7 +491,6 @@ struct SweepArgs {
     int *clear;                 // next step's bin counts to zero, or NULL
     int *err;                   // the lattice's error word
     FieldsOut fo;               // MODE_FIELDS outputs
-    int pre;                    // candidates whose records come with the stage: 0 or PRE_C
 };
 
 // A batched sweep walks one work list over many lattices, their descriptors
@@ -523,7 +505,6 @@ struct BatchArgs {
     int item_start[BATCH_LAUNCH_MAX + 1];
     int tile_start[BATCH_LAUNCH_MAX + 1];
     int n;
-    int pre;                    // as SweepArgs::pre, for every member
 };
 static_assert(sizeof(BatchArgs<float>) <= 32000, "batched sweep parameters exceed the parameter space");
 
@@ -558,8 +539,8 @@ struct Ring {
 // when there is one, then stream, collide, store and sum the segment's
 // force / torque.  Returns false if the bounded wait gave up.
 template <typename T, int MODE, bool EDGES>
-__device__ __forceinline__ bool sweep_segment(const SweepArgs<T> &A, int pre, int y, int tx, T *stage, Ring &ring,
-                                              int s, bool has_next, const SweepArgs<T> &An, int ny2, int nx2,
+__device__ __forceinline__ bool sweep_segment(const SweepArgs<T> &A, int y, int tx, T *stage, Ring &ring, int s,
+                                              bool has_next, const SweepArgs<T> &An, int ny2, int nx2,
                                               float4 *crec, int *cid, int lane) {
     constexpr int H = halo_of<T>(), SW = segw_of<T>();
     const Lattice &L = A.L;
@@ -568,34 +549,26 @@ __device__ __forceinline__ bool sweep_segment(const SweepArgs<T> &A, int pre, in
     const int tx0 = tx * TILE_W, ty0 = ty * TILE_H;
     const int x0 = tx0 + lane * VEC;
 
+    // ---- the tile's candidate particles (records written by the binning),
+    // loaded before the wait so that their latency overlaps it
+    __syncwarp();
+    int ncand = 0;
+    if (A.B.count) {
+        ncand = A.B.count[tile];
+        ncand = ncand > MAXC ? MAXC : ncand;
+        if (lane < ncand) {
+            const long long r = (long long)tile * MAXC + lane;
+#pragma unroll
+            for (int q = 0; q < NREC; ++q) crec[q * MAXC + lane] = A.B.rec[NREC * r + q];
+            cid[lane] = A.B.ids[r];
+        }
+    }
+
     // ---- wait for the staged rows and tile header
     // a warp-uniform decision: every lane leaves together if any gave up
-    __syncwarp();
     if (!__all_sync(0xffffffffu, mbar_wait_bounded(&ring.bars[s], (ring.parity >> s) & 1u))) return false;
     ring.parity ^= 1u << s;
     ring.pending &= ~(1u << s);
-
-    // ---- the tile's candidate particles (records written by the binning):
-    // the first PRE_C came with the stage, any further ones from global memory
-    int ncand = 0;
-    if (A.B.count) {
-        const unsigned char *h = reinterpret_cast<const unsigned char *>(stage + 9 * SW);
-        ncand = reinterpret_cast<const int *>(h)[tile & 3];
-        ncand = ncand > MAXC ? MAXC : ncand;
-        if (lane < ncand) {
-            if (lane < pre) {
-                const float4 *pr = reinterpret_cast<const float4 *>(h + HDR_RECS);
-#pragma unroll
-                for (int q = 0; q < NREC; ++q) crec[q * MAXC + lane] = pr[lane * NREC + q];
-                cid[lane] = reinterpret_cast<const int *>(h + HDR_IDS)[lane];
-            } else {
-                const long long r = (long long)tile * MAXC + lane;
-#pragma unroll
-                for (int q = 0; q < NREC; ++q) crec[q * MAXC + lane] = A.B.rec[NREC * r + q];
-                cid[lane] = A.B.ids[r];
-            }
-        }
-    }
 
     // ---- pull-stream from the staged rows: f_i(x, t+1) = f'_i(x - c_i, t)
     const int c0 = H + lane * VEC;
@@ -610,40 +583,20 @@ __device__ __forceinline__ bool sweep_segment(const SweepArgs<T> &A, int pre, in
     }
     const bool row_edge = EDGES && !L.per_y && (y == 0 || y == L.ny - 1);
     const bool col_edge = EDGES && !L.per_x && (tx == 0 || tx0 + TILE_W >= L.nx);
-    // west / east edge nodes of a row that is not itself an edge row take
-    // the inner neighbour's (x + 1 or x - 1, same row) streamed values: from
-    // this thread's registers, from the left lane's, or -- for an east edge
-    // that opens its segment (nx = 1 mod 128) -- pulled from the staged halo,
-    // which is why this runs before the stage is recycled
-    if (col_edge && !row_edge) {
-        float left[9];
+    // an east edge that opens its segment (nx = 1 mod 128, lane 0) has its
+    // inner neighbour in the previous segment: pull that neighbour's values
+    // from the staged halo before the stage is recycled, into the slot of
+    // node x0 + 1, which lies past the edge and is never stored
+    if (col_edge && !row_edge && lane == 0 && x0 == L.nx - 1) {
 #pragma unroll
-        for (int i = 0; i < 9; ++i) left[i] = __shfl_up_sync(0xffffffffu, d[i][VEC - 1], 1);
-        if (lane == 0 && x0 == L.nx - 1) {
-#pragma unroll
-            for (int i = 0; i < 9; ++i)
-                left[i] = from_store<T>(L, i, Storage<T>::lds1(stage + i * SW + (c0 - 1 - cxof(i))));
-        }
-#pragma unroll
-        for (int q = 0; q < VEC; ++q) {
-            const int x = x0 + q;
-            if (x != 0 && x != L.nx - 1) continue;
-            float dn[9], e[9];
-#pragma unroll
-            for (int i = 0; i < 9; ++i) {
-                if (x == 0) dn[i] = d[i][q < VEC - 1 ? q + 1 : q];            // q == 0 here: x0 == 0
-                else dn[i] = q > 0 ? d[i][q > 0 ? q - 1 : 0] : left[i];
-            }
-            extrapolate(L, x == 0 ? WEST : EAST, dn, e);
-#pragma unroll
-            for (int i = 0; i < 9; ++i) d[i][q] = e[i];
-        }
+        for (int i = 0; i < 9; ++i)
+            d[i][1] = from_store<T>(L, i, Storage<T>::lds1(stage + i * SW + (c0 - 1 - cxof(i))));
     }
     __syncwarp();
     // recycle the stage for the segment STAGES items ahead
     if (has_next) {
         fence_proxy_async_smem();
-        issue_segment<T>(An.src, An.L, An.B, pre, ny2, nx2, stage, &ring.bars[s], lane);
+        issue_segment<T>(An.src, An.L, ny2, nx2, stage, &ring.bars[s], lane);
         ring.pending |= 1u << s;
     }
     // periodic x: the row's first node pulls from column nx-1 and its
@@ -663,6 +616,32 @@ __device__ __forceinline__ bool sweep_segment(const SweepArgs<T> &A, int pre, in
             }
         }
     }
+    // west / east edge nodes of a row that is not itself an edge row take
+    // the inner neighbour's (x + 1 or x - 1, same row) streamed values: from
+    // this thread's registers, from the left lane's, or (east edge opening
+    // its segment) from the slot filled from the halo above
+    if (col_edge && !row_edge) {
+        float left[9];
+#pragma unroll
+        for (int i = 0; i < 9; ++i) {
+            left[i] = __shfl_up_sync(0xffffffffu, d[i][VEC - 1], 1);
+            if (lane == 0) left[i] = d[i][1];
+        }
+#pragma unroll
+        for (int q = 0; q < VEC; ++q) {
+            const int x = x0 + q;
+            if (x != 0 && x != L.nx - 1) continue;
+            float dn[9], e[9];
+#pragma unroll
+            for (int i = 0; i < 9; ++i) {
+                if (x == 0) dn[i] = d[i][q < VEC - 1 ? q + 1 : q];            // q == 0 here: x0 == 0
+                else dn[i] = q > 0 ? d[i][q > 0 ? q - 1 : 0] : left[i];
+            }
+            extrapolate(L, x == 0 ? WEST : EAST, dn, e);
+#pragma unroll
+            for (int i = 0; i < 9; ++i) d[i][q] = e[i];
+        }
+    }
     __syncwarp();   // candidate records visible to the whole warp
 
     // ---- solid fraction (Eq. 14), owner and particle velocity per node:
@@ -672,7 +651,6 @@ __device__ __forceinline__ bool sweep_segment(const SweepArgs<T> &A, int pre, in
 #pragma unroll
     for (int q = 0; q < VEC; ++q) { phi[q] = 0.f; rxn[q] = 0.f; ryn[q] = 0.f; best[q] = -1; best_id[q] = 0x7fffffff; }
     // (ncand is warp-uniform; a segment no particle reaches skips all of it)
-    const float inv_nx = 1.0f / (float)L.nx, inv_ny = 1.0f / (float)L.ny;
     for (int c = 0; c < ncand; ++c) {
         const float4 ra = crec[c], rb = crec[MAXC + c];
         const float R = rb.x + ph.cut;
@@ -680,7 +658,7 @@ __device__ __forceinline__ bool sweep_segment(const SweepArgs<T> &A, int pre, in
         // short periodic axes: the stored image may lie several periods away
         // (it is the one nearest the tile centre), so reduce by the nearest
         // multiple of the period (exact: an integer multiple of an integer)
-        if (L.wrap_y) dy = fmaf(-(float)L.ny, rintf(dy * inv_ny), dy);
+        if (L.wrap_y) dy = fmaf(-(float)L.ny, rintf(dy * __frcp_rn((float)L.ny)), dy);
         const float h2 = R * R - dy * dy;
         if (h2 < 0.f) continue;                         // this row misses the disc tail
         const float dx0 = ((float)(x0 - tx0) - ra.x) - ra.y;
@@ -693,7 +671,7 @@ __device__ __forceinline__ bool sweep_segment(const SweepArgs<T> &A, int pre, in
 #pragma unroll
         for (int q = 0; q < VEC; ++q) {
             float dx = dx0 + (float)q;
-            if (L.wrap_x) dx = fmaf(-(float)L.nx, rintf(dx * inv_nx), dx);
+            if (L.wrap_x) dx = fmaf(-(float)L.nx, rintf(dx * __frcp_rn((float)L.nx)), dx);
             const float d2 = dx * dx + dy * dy;
             if (d2 > R * R) continue;
             const float l = rb.x - sqrtf(d2);
@@ -834,8 +812,10 @@ __device__ __forceinline__ bool sweep_segment(const SweepArgs<T> &A, int pre, in
     if (MODE == MODE_FIELDS) return true;
     if (__any_sync(0xffffffffu, badmax > 0x7f7ffffeu) && lane == 0) atomicOr(A.err, ERR_UNSTABLE);
 
-    // ---- store the collided populations
-    {
+    // ---- store the collided populations.  Without edge code one branch for
+    // the whole segment; with it the per-direction form, which measured
+    // faster in that larger kernel (its code layout is sensitive)
+    if (!EDGES) {
         T *base = A.dst + (long long)y * L.pitch + x0;
         if (x0 + VEC <= L.nx) {
 #pragma unroll
@@ -849,6 +829,21 @@ __device__ __forceinline__ bool sweep_segment(const SweepArgs<T> &A, int pre, in
 #pragma unroll
                 for (int q = 0; q < VEC; ++q)
                     if (x0 + q < L.nx) Storage<T>::store1(base + i * L.plane + q, vv[q]);
+            }
+        }
+    } else {
+        const bool full = x0 + VEC <= L.nx;
+#pragma unroll
+        for (int i = 0; i < 9; ++i) {
+            T *row = A.dst + i * L.plane + (long long)y * L.pitch;
+            const float4 v = to_store4<T>(L, i, make_float4(d[i][0], d[i][1], d[i][2], d[i][3]));
+            if (full) {
+                Storage<T>::store4(row + x0, v);
+            } else {
+                const float vv[VEC] = {v.x, v.y, v.z, v.w};
+#pragma unroll
+                for (int q = 0; q < VEC; ++q)
+                    if (x0 + q < L.nx) Storage<T>::store1(row + x0 + q, vv[q]);
             }
         }
     }
@@ -938,8 +933,7 @@ sweep_kernel(const __grid_constant__ SweepArgs<T> one)
         int py = y, ptx = tx;
         for (int s = 0; s < STAGES; ++s) {
             if (gw + s * nw < nitems) {
-                issue_segment<T>(one.src, L, one.B, one.pre, py, ptx, sm.stages + s * stage_elems<T>(), &ring.bars[s],
-                                 lane);
+                issue_segment<T>(one.src, L, py, ptx, sm.stages + s * stage_elems<T>(), &ring.bars[s], lane);
                 ring.pending |= 1u << s;
             }
             advance(py, ptx);
@@ -958,7 +952,7 @@ sweep_kernel(const __grid_constant__ SweepArgs<T> one)
         }
         const int s = k % STAGES;
         const bool has_next = item + STAGES * nw < nitems;
-        if (!sweep_segment<T, MODE, EDGES>(one, one.pre, y, tx, sm.stages + s * stage_elems<T>(), ring, s, has_next, one, ay, atx,
+        if (!sweep_segment<T, MODE, EDGES>(one, y, tx, sm.stages + s * stage_elems<T>(), ring, s, has_next, one, ay, atx,
                                            sm.crec, sm.cid, lane)) {
             timed_out = true;
             break;
@@ -1025,7 +1019,7 @@ sweep_batch_kernel(const __grid_constant__ BatchArgs<T> ba)
         const int it = gw + s * nw;
         if (it < nitems) {
             cursor_seek(ba, ahead, it);
-            issue_segment<T>(ba.a[ahead.lat].src, ba.a[ahead.lat].L, ba.a[ahead.lat].B, ba.pre, ahead.y, ahead.tx,
+            issue_segment<T>(ba.a[ahead.lat].src, ba.a[ahead.lat].L, ahead.y, ahead.tx,
                              sm.stages + s * stage_elems<T>(), &ring.bars[s], lane);
             ring.pending |= 1u << s;
         }
@@ -1042,8 +1036,8 @@ sweep_batch_kernel(const __grid_constant__ BatchArgs<T> ba)
         const bool has_next = nxt < nitems;
         if (has_next) cursor_seek(ba, ahead, nxt);
         const int nlat = has_next ? ahead.lat : cur.lat;
-        if (!sweep_segment<T, MODE, true>(ba.a[cur.lat], ba.pre, cur.y, cur.tx, sm.stages + s * stage_elems<T>(), ring,
-                                          s, has_next, ba.a[nlat], ahead.y, ahead.tx, sm.crec, sm.cid, lane)) {
+        if (!sweep_segment<T, MODE, true>(ba.a[cur.lat], cur.y, cur.tx, sm.stages + s * stage_elems<T>(), ring, s,
+                                          has_next, ba.a[nlat], ahead.y, ahead.tx, sm.crec, sm.cid, lane)) {
             timed_out = true;
             break;
         }

@@ -16,14 +16,12 @@ namespace dilbm {
 struct SweepShape {
     int warps = SWEEP_WARPS;    // rows in flight per block: 2, 4 or 8
     int blocks_per_sm = 0;      // persistent blocks per SM; 0: as many as fit
-    int prefetch = PRE_C;       // candidate records staged with each row segment: 0 or PRE_C
 };
 
 constexpr int SHAPE_WARPS[3] = {2, 4, 8};
 
 __host__ inline bool shape_valid(const SweepShape &s) {
-    return (s.warps == 2 || s.warps == 4 || s.warps == 8) && s.blocks_per_sm >= 0 &&
-           (s.prefetch == 0 || s.prefetch == PRE_C);
+    return (s.warps == 2 || s.warps == 4 || s.warps == 8) && s.blocks_per_sm >= 0;
 }
 
 // Blocks of `kern` (W warps, `smem` bytes of dynamic shared memory) resident
@@ -69,9 +67,7 @@ cudaError_t step_variant(const SweepArgs<T> &a, const SweepShape &sh, int num_sm
     }
     const long long items = (long long)a.L.ny * a.L.ntx;
     const long long blocks = persistent_grid(items, W, per_sm, num_sms, sh);
-    SweepArgs<T> ap = a;
-    ap.pre = sh.prefetch;
-    sweep_kernel<T, MODE_STEP, EDGES, W><<<(unsigned)blocks, W * 32, smem, st>>>(ap);
+    sweep_kernel<T, MODE_STEP, EDGES, W><<<(unsigned)blocks, W * 32, smem, st>>>(a);
     return cudaGetLastError();
 }
 
@@ -87,14 +83,7 @@ cudaError_t batch_variant(const BatchArgs<T> &ba, const SweepShape &sh, int num_
         return e;
     }
     const long long blocks = persistent_grid(ba.item_start[ba.n], W, per_sm, num_sms, sh);
-    if (ba.pre == sh.prefetch) {
-        sweep_batch_kernel<T, MODE_STEP, W><<<(unsigned)blocks, W * 32, smem, st>>>(ba);
-    } else {
-        BatchArgs<T> *bp = new BatchArgs<T>(ba);    // a candidate of the autotuner
-        bp->pre = sh.prefetch;
-        sweep_batch_kernel<T, MODE_STEP, W><<<(unsigned)blocks, W * 32, smem, st>>>(*bp);
-        delete bp;
-    }
+    sweep_batch_kernel<T, MODE_STEP, W><<<(unsigned)blocks, W * 32, smem, st>>>(ba);
     return cudaGetLastError();
 }
 

@@ -247,7 +247,6 @@ extern "C" int dilbm_step_static(const dilbm_grid *g, double tau, double interfa
     sa.partial = partial;
     sa.clear = np > 0 ? bins[1].count : nullptr;
     sa.err = err;
-    sa.pre = PRE_C;
     if (L.per_x && L.per_y) {
         S_CUDA(cudaFuncSetAttribute(sweep_kernel<float, MODE_STEP, false>,
                                     cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));

@@ -127,10 +127,10 @@ def load_library(path: Optional[str] = None):
     L.dilbm_batch_destroy.restype = None
     L.dilbm_batch_errors.argtypes = [vp, C.POINTER(C.c_int)]
     ipp = C.POINTER(C.c_int)
-    L.dilbm_autotune.argtypes = [vp, ip, ipp, ipp, ipp]
-    L.dilbm_set_shape.argtypes = [vp, ip, ip, ip]
-    L.dilbm_batch_autotune.argtypes = [vp, ip, ipp, ipp, ipp]
-    L.dilbm_batch_set_shape.argtypes = [vp, ip, ip, ip]
+    L.dilbm_autotune.argtypes = [vp, ip, ipp, ipp]
+    L.dilbm_set_shape.argtypes = [vp, ip, ip]
+    L.dilbm_batch_autotune.argtypes = [vp, ip, ipp, ipp]
+    L.dilbm_batch_set_shape.argtypes = [vp, ip, ip]
     L.dilbm_footprint.argtypes = [C.POINTER(Grid), ip, C.POINTER(C.c_ulonglong)]
     L.dilbm_server_create.argtypes = [C.POINTER(ServerConfig), vp, C.POINTER(vp)]
     L.dilbm_server_submit.argtypes = [vp, C.POINTER(Job), C.POINTER(C.c_longlong)]
@@ -315,13 +315,13 @@ class Simulation:
     # -- launch shape
     def autotune(self, reps: int = 10):
         """Time the candidate sweep shapes on this lattice, keep the fastest;
-        returns (warps per block, blocks per SM, prefetch)."""
-        w, b, p = C.c_int(), C.c_int(), C.c_int()
-        check(self.L.dilbm_autotune(self.h, int(reps), C.byref(w), C.byref(b), C.byref(p)))
-        return w.value, b.value, p.value
+        returns (warps per block, blocks per SM)."""
+        w, b = C.c_int(), C.c_int()
+        check(self.L.dilbm_autotune(self.h, int(reps), C.byref(w), C.byref(b)))
+        return w.value, b.value
 
-    def set_shape(self, warps: int, blocks_per_sm: int = 0, prefetch: int = 8) -> None:
-        check(self.L.dilbm_set_shape(self.h, int(warps), int(blocks_per_sm), int(prefetch)))
+    def set_shape(self, warps: int, blocks_per_sm: int = 0) -> None:
+        check(self.L.dilbm_set_shape(self.h, int(warps), int(blocks_per_sm)))
 
     # -- measurement
     def set_timing(self, on: bool) -> None:
@@ -372,12 +372,12 @@ class Batch:
             raise DilbmError(rc, f"member {bad.value}: " + self.L.dilbm_last_error().decode(errors="replace"))
 
     def autotune(self, reps: int = 10):
-        w, b, p = C.c_int(), C.c_int(), C.c_int()
-        check(self.L.dilbm_batch_autotune(self.h, int(reps), C.byref(w), C.byref(b), C.byref(p)))
-        return w.value, b.value, p.value
+        w, b = C.c_int(), C.c_int()
+        check(self.L.dilbm_batch_autotune(self.h, int(reps), C.byref(w), C.byref(b)))
+        return w.value, b.value
 
-    def set_shape(self, warps: int, blocks_per_sm: int = 0, prefetch: int = 8) -> None:
-        check(self.L.dilbm_batch_set_shape(self.h, int(warps), int(blocks_per_sm), int(prefetch)))
+    def set_shape(self, warps: int, blocks_per_sm: int = 0) -> None:
+        check(self.L.dilbm_batch_set_shape(self.h, int(warps), int(blocks_per_sm)))
 
     def set_timing(self, on: bool) -> None:
         check(self.L.dilbm_batch_set_timing(self.h, 1 if on else 0))
