@@ -156,6 +156,29 @@ def max_over_ranks(dist, value, device=None):
     return float(t.item())
 
 
+def sum_over_ranks(dist, value, device=None):
+    if dist is None:
+        return value
+    import torch
+    t = torch.tensor([value], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.SUM)
+    return float(t.item())
+
+
+def gather_lists(dist, items):
+    """Every rank's list, concatenated in rank order (the list itself at N=1)."""
+    if dist is None:
+        return list(items)
+    out = [None] * dist.get_world_size()
+    dist.all_gather_object(out, list(items))
+    return [v for part in out for v in part]
+
+
+def shard(items, rank, world):
+    """Rank ``rank``'s share of independent work items (every world-th)."""
+    return list(items)[rank::world]
+
+
 def barrier(dist):
     if dist is not None:
         dist.barrier()
@@ -339,7 +362,7 @@ def gpu_arm(args):
                                          "by": "--shape" if args.shape else "autotuner"},
                            l2="populations 9x2 planes exceed L2; no flush",
                            parallelism=f"replicas x{world}" if world > 1 else "single GPU"),
-            "roofline": roof, "gpu_launches": launches, "e2e": e2e, "clocks": clk}
+            "roofline": roof, "gpu_launches": int(sum_over_ranks(dist, launches, dev)), "e2e": e2e, "clocks": clk}
 
     # ---- the oracle on the host cores, rank 0 at N=1 only
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
@@ -394,7 +417,8 @@ def batch_arm(args):
     launches = batch.launches - l0
     clk = clocks.stop()
     dt = max_over_ranks(dist, dt, dev)
-    value = nodes * args.steps * world / dt / 1e6
+    total_nodes = sum_over_ranks(dist, nodes, dev)        # each rank has its own lattices
+    value = total_nodes * args.steps / dt / 1e6
 
     # the batched sweep alone, timed by CUDA events (direct launches)
     k_t = max(10, min(args.steps, 200))
@@ -416,7 +440,8 @@ def batch_arm(args):
     for a in alone:
         a.sync()
     dt_alone = time.perf_counter() - t0
-    alone_value = nodes * k_alone / dt_alone / 1e6
+    dt_alone = max_over_ranks(dist, dt_alone, dev)
+    alone_value = total_nodes * k_alone / dt_alone / 1e6
 
     peak, peak_kind = measured_peak_hbm()
     per_launch = sweep_ms / max(sweep_n, 1)
@@ -429,7 +454,7 @@ def batch_arm(args):
             "data": "synthetic",
             "config": {"workload": "batch of 64 uneven lattices (seed 4): nx log-U[128,1024], ny log-U[128,2048], "
                                    "cylinder or sedimentation jobs, 1-32 discs r U[5,15], Re log-U[10,100]",
-                       "storage": args.storage, "nodes": nodes, "lattices": len(jobs),
+                       "storage": args.storage, "nodes": nodes, "nodes_all_ranks": total_nodes, "lattices": len(jobs),
                        "particles": sum(len(j.particles) for j in jobs),
                        "launch": "one batched sweep + one batched particle launch per step, CUDA-graph replay",
                        "launch_shape": {"warps_per_block": shape[0], "blocks_per_sm": shape[1],
@@ -440,7 +465,7 @@ def batch_arm(args):
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
                          "traffic": None, "peak_kind": peak_kind, "kernel": "sweep_kernel (batched)",
                          "sweep_ms_per_launch": per_launch, "algorithmic_bytes_per_launch": alg},
-            "gpu_launches": launches, "e2e": None, "clocks": clk}
+            "gpu_launches": int(sum_over_ranks(dist, launches, dev)), "e2e": None, "clocks": clk}
     if rank == 0:
         print(json.dumps(line), flush=True)
     for a in alone:
@@ -542,8 +567,9 @@ def serve_arm(args):
     dist = init_dist(world, "nccl")
     dev = torch.device("cuda", local)
     # replicas: rank k serves every world-th request of the stream
-    reqs = W.request_stream(count=args.requests * world)[rank::world]
+    reqs = shard(W.request_stream(count=args.requests * world), rank, world)
     work = sum(r.problem.nx * r.problem.ny * r.steps for r in reqs)
+    total_work = sum_over_ranks(dist, work, dev)        # node updates of all ranks' requests
     stream = torch.cuda.Stream(device=dev)
     sh = int(stream.cuda_stream)
     # warm-up: one small job through each path (module load, graph capture)
@@ -570,27 +596,30 @@ def serve_arm(args):
     clk = clocks.stop()
 
     def summary(a):
-        lv = list(a["lat"].values())
-        out = {"value": work * world / a["span"] / 1e6, "unit": "MLUPS", "p50_s": percentile(lv, 50),
-               "p99_s": percentile(lv, 99), "makespan_s": a["span"], "gpu_launches": a["launches"]}
+        lv = gather_lists(dist, a["lat"].values())          # every rank's requests
+        out = {"value": total_work / a["span"] / 1e6, "unit": "MLUPS", "p50_s": percentile(lv, 50),
+               "p99_s": percentile(lv, 99), "makespan_s": a["span"],
+               "gpu_launches": int(sum_over_ranks(dist, a["launches"], dev))}
         if "host" in a:
             out["server_time"] = a["host"]
         return out
 
     s16, s32, s1 = summary(arms["served_fp16"]), summary(arms["served_fp32"]), summary(arms["single_fp32"])
     d16, r16 = drag_errors(reqs, arms["served_fp16"]["res"], arms["served_fp32"]["res"])
+    d16, r16 = gather_lists(dist, d16), gather_lists(dist, r16)
     parts_in = sum(len(r.problem.particles) for r in reqs)
     import numpy as np
     same = all(np.array_equal(arms["served_fp32"]["res"][k][0], arms["single_fp32"]["res"][k][0]) and
                np.array_equal(arms["served_fp32"]["res"][k][2], arms["single_fp32"]["res"][k][2])
                for k in range(len(reqs)))
+    same = sum_over_ranks(dist, 0.0 if same else 1.0, dev) == 0.0
     line = {"metric": METRIC, "value": s16["value"], "unit": "MLUPS", "n_gpus": world, "steps": len(reqs),
             "warmup": 1, "ms_per_step": None, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
             "dtype": "f16-storage/f32-math", "data": "synthetic",
             "config": {"workload": f"served: the first {len(reqs) * world} requests of a Poisson stream "
                                    "(seed 5, 50 requests/s): cylinder or sedimentation jobs, nx, ny log-U[128,2048], "
                                    "1-64 discs r U[5,15], steps log-U[1k,20k]; replayed in real time",
-                       "storage": "fp16", "node_updates": work * world, "max_jobs": args.max_jobs,
+                       "storage": "fp16", "node_updates": total_work, "max_jobs": args.max_jobs,
                        "macro_steps": args.macro_steps, "admission": "FIFO by job slots and free device memory",
                        "l2": "resident lattices exceed L2 once a few large jobs run; no flush",
                        "parallelism": f"replicas x{world}" if world > 1 else "single GPU"},
