@@ -38,6 +38,18 @@
  *     the collision hands to the fluid, -sum_i c_i (f'_i - f_i);
  *   - initial populations are f^eq(rho_init, u0) everywhere.
  *
+ * method 1 replaces steps 1, 4-8 by the paper's comparison method, the
+ * partially saturated LBM with the SP collision (Sec. 2.2):
+ *   1'. solid volume fraction eps_s of every node's unit cell, the exact area
+ *       of the cell covered by the disc (the paper requires it and gives no
+ *       algorithm: here the integral of the covered chord length over the
+ *       cell's width, in closed form), B = eps_s (Eq. 8);
+ *   5'-7'. f' = f + (1 - B)(-(f - f^eq(rho, u*))/tau) + B Omega^s with the
+ *       additional collision term Omega^s of Eq. 9 (f^eq takes the fluid
+ *       velocity u*: there is no correction step);
+ *   8'. force and torque by the double sums of Eqs. 10-11.
+ * The same max rule picks a node's owner (the largest covered fraction).
+ *
  * Memory layout: populations f[i][y][x], x fastest, i = 0..8 in the order of
  * Eq. 3: (0,0) (1,0) (0,1) (-1,0) (0,-1) (1,1) (-1,1) (-1,-1) (1,-1).
  */
@@ -73,6 +85,7 @@ typedef struct {
     double eps_p, eps_p2, eps_w, eps_w2, xi;  /* Eqs. 28-29 */
     double phi_cutoff;           /* 0: every particle at every node; > 0: a particle
                                     reaches only nodes with l >= -phi_cutoff */
+    int method;                  /* 0: DI-LBM (Eq. 13); 1: PS-LBM with the SP collision (Eqs. 7-11) */
 } orc_params;
 
 typedef struct {
@@ -167,6 +180,90 @@ void orc_collide_node(double tau, const double f[9], double phi, double usx_, do
     for (int i = 0; i < 9; ++i)                  /* Eq. 13 */
         fout[i] = f[i] - (f[i] - feq[i]) / tau + phi * Fi[i];
     mom[0] = rho; mom[1] = uax; mom[2] = uay; mom[3] = ux; mom[4] = uy;
+}
+
+/* Solid volume fraction for the PS-LBM (Sec. 2.2): the area of the unit cell
+ * [dx - 1/2, dx + 1/2] x [dy - 1/2, dy + 1/2] covered by the disc of radius r
+ * centred at the origin.  The area is the integral over the cell's width of
+ * the covered length of the vertical line at x,
+ *   L(x) = max(0, min(y1, h(x)) - max(y0, -h(x))),  h(x) = sqrt(r^2 - x^2),
+ * which on each piece between the abscissae where h crosses y0 or y1 is
+ * 0, y1 - y0, h - y0, y1 + h or 2h; the integral of h has the closed form
+ * (x h + r^2 asin(x / r)) / 2.  h is formed as sqrt((r - x)(r + x)) and
+ * asin(x / r) as atan2(x, h), which stay accurate where x approaches r. */
+static double half_chord(double x, double r) { return sqrt((r - x) * (r + x)); }
+
+static double int_h(double x, double r)
+{
+    if (x <= -r) return -0.25 * M_PI * r * r;
+    if (x >= r) return 0.25 * M_PI * r * r;
+    double h = half_chord(x, r);
+    return 0.5 * (x * h + r * r * atan2(x, h));
+}
+
+double orc_cell_fraction(double dx, double dy, double r)
+{
+    double x0 = dx - 0.5, x1 = dx + 0.5, y0 = dy - 0.5, y1 = dy + 0.5;
+    if (x0 < -r) x0 = -r;
+    if (x1 > r) x1 = r;
+    if (x0 >= x1) return 0.0;
+    /* breakpoints: |x| where h(x) = |y0| or |y1| */
+    double br[6];
+    int nb = 0;
+    br[nb++] = x0;
+    const double ys[2] = {y0, y1};
+    for (int k = 0; k < 2; ++k) {
+        if (fabs(ys[k]) < r) {
+            double xb = half_chord(fabs(ys[k]), r);
+            if (xb > x0 && xb < x1) br[nb++] = xb;
+            if (-xb > x0 && -xb < x1) br[nb++] = -xb;
+        }
+    }
+    br[nb++] = x1;
+    for (int a = 1; a < nb; ++a)              /* sort the few breakpoints */
+        for (int b = a; b > 0 && br[b] < br[b - 1]; --b) {
+            double t = br[b]; br[b] = br[b - 1]; br[b - 1] = t;
+        }
+    double area = 0.0;
+    for (int k = 0; k + 1 < nb; ++k) {
+        double a = br[k], b = br[k + 1];
+        if (b <= a) continue;
+        double xm = 0.5 * (a + b), hm = half_chord(xm, r);
+        /* with no breakpoint inside the piece, h - y1 and h + y0 keep their
+         * sign on it (<=: a circle tangent to y1 at x = 0 touches it there only) */
+        int top = hm <= y1;        /* the disc's upper edge lies inside the cell on this piece */
+        int bot = -hm >= y0;       /* the lower edge does */
+        double lo = bot ? -hm : y0, hi = top ? hm : y1;
+        if (hi <= lo) continue;    /* the line misses the covered part */
+        double ih = int_h(b, r) - int_h(a, r);
+        if (top && bot) area += 2.0 * ih;
+        else if (top) area += ih - y0 * (b - a);
+        else if (bot) area += y1 * (b - a) + ih;
+        else area += (y1 - y0) * (b - a);
+    }
+    return area;
+}
+
+/* Eq. 7 with the SP term Omega^s of Eq. 9 (B = eps_s, Eq. 8) at one node.
+ * omega_s receives Omega^s; mom receives rho, u*x, u*y. */
+void orc_collide_node_ps(double tau, const double f[9], double B, double usx_, double usy_,
+                         double fout[9], double omega_s[9], double mom[3])
+{
+    double rho = 0.0, jx = 0.0, jy = 0.0;
+    for (int i = 0; i < 9; ++i) {
+        rho += f[i];
+        jx += CX[i] * f[i];
+        jy += CY[i] * f[i];
+    }
+    double ux = jx / rho, uy = jy / rho;
+    double feq[9], feqs[9];
+    orc_equilibrium(rho, ux, uy, feq);
+    orc_equilibrium(rho, usx_, usy_, feqs);
+    for (int i = 0; i < 9; ++i) {
+        omega_s[i] = feqs[i] - f[i] + (1.0 - 1.0 / tau) * (f[i] - feq[i]);
+        fout[i] = f[i] + (1.0 - B) * (-(f[i] - feq[i]) / tau) + B * omega_s[i];
+    }
+    mom[0] = rho; mom[1] = ux; mom[2] = uy;
 }
 
 /* Eqs. 28-29: Wan-Turek repulsion on every particle from the others and from
@@ -336,11 +433,46 @@ static void solid_fraction_cutoff(orc_sim *s)
     for (long long k = 0; k < (long long)n; ++k) set_particle_velocity(s, (size_t)k);
 }
 
+/* Step 1' (PS-LBM): B = eps_s, owner and u_s at every node.  A disc covers
+ * no part of a cell whose centre is farther than r + sqrt(2)/2, so only
+ * nearer particles are evaluated (this skips nothing). */
+static void solid_fraction_ps(orc_sim *s)
+{
+    const orc_params *p = &s->p;
+    int nx = p->nx, ny = p->ny;
+#pragma omp parallel for schedule(static)
+    for (int y = 0; y < ny; ++y) {
+        for (int x = 0; x < nx; ++x) {
+            size_t k = (size_t)y * nx + x;
+            double best = 0.0, brx = 0.0, bry = 0.0;
+            int own = -1;
+            for (int q = 0; q < s->np; ++q) {
+                const orc_particle *P = &s->parts[q];
+                double dx = x - P->x, dy = y - P->y;
+                if (periodic_x(p)) dx = min_image(dx, nx);
+                if (periodic_y(p)) dy = min_image(dy, ny);
+                if (sqrt(dx * dx + dy * dy) > P->r + 0.7072) continue;
+                double e = orc_cell_fraction(dx, dy, P->r);
+                if (e > best) { best = e; own = q; brx = dx; bry = dy; }
+            }
+            s->phi[k] = best;
+            s->owner[k] = own;
+            s->rx[k] = brx;
+            s->ry[k] = bry;
+            set_particle_velocity(s, k);
+        }
+    }
+}
+
 /* Step 1: phi, owner and u_s at every node from the current particle state. */
 static void solid_fraction(orc_sim *s)
 {
     const orc_params *p = &s->p;
     int nx = p->nx, ny = p->ny;
+    if (p->method == 1) {
+        solid_fraction_ps(s);
+        return;
+    }
     if (p->phi_cutoff > 0.0) {
         solid_fraction_cutoff(s);
         return;
@@ -479,9 +611,23 @@ int orc_step(orc_sim *s, long long nsteps)
                 size_t k = (size_t)y * nx + x;
                 double f[9], fo[9], Fi[9], mom[5];
                 for (int i = 0; i < 9; ++i) f[i] = s->fpre[i * n + k];
+                double gx = 0.0, gy = 0.0;
+                if (p->method == 1) {               /* PS-LBM: Eq. 7, force of Eq. 10 */
+                    orc_collide_node_ps(p->tau, f, s->phi[k], s->usx[k], s->usy[k], fo, Fi, mom);
+                    if (!(mom[0] > 0.0) || !isfinite(mom[1]) || !isfinite(mom[2])) bad = 1;
+                    for (int i = 0; i < 9; ++i) {
+                        gx += Fi[i] * CX[i];
+                        gy += Fi[i] * CY[i];
+                    }
+                    gx *= -s->phi[k];
+                    gy *= -s->phi[k];
+                    s->gx[k] = gx;
+                    s->gy[k] = gy;
+                    for (int i = 0; i < 9; ++i) s->f[i * n + k] = fo[i];
+                    continue;
+                }
                 orc_collide_node(p->tau, f, s->phi[k], s->usx[k], s->usy[k], fo, Fi, mom);
                 if (!(mom[0] > 0.0) || !isfinite(mom[1]) || !isfinite(mom[2])) bad = 1;
-                double gx = 0.0, gy = 0.0;
                 if (p->force_model == 0) {          /* Eq. 18 as printed */
                     for (int i = 0; i < 9; ++i) {
                         gx += Fi[i] * CX[i];
@@ -524,8 +670,10 @@ void orc_fields(orc_sim *s, double *rho, double *ux, double *uy, double *phi, in
         }
         double uax = jx / r, uay = jy / r;
         if (rho) rho[k] = r;
-        if (ux) ux[k] = uax + 0.5 * s->phi[k] * (s->usx[k] - uax);
-        if (uy) uy[k] = uay + 0.5 * s->phi[k] * (s->usy[k] - uay);
+        /* DI: the corrected velocity of Eq. 17; PS: the fluid velocity u* */
+        double c = p->method == 1 ? 0.0 : 0.5 * s->phi[k];
+        if (ux) ux[k] = uax + c * (s->usx[k] - uax);
+        if (uy) uy[k] = uay + c * (s->usy[k] - uay);
         if (phi) phi[k] = s->phi[k];
         if (owner) owner[k] = s->owner[k];
     }

@@ -36,6 +36,7 @@ class OrcParams(C.Structure):
         ("eps_p", C.c_double), ("eps_p2", C.c_double), ("eps_w", C.c_double),
         ("eps_w2", C.c_double), ("xi", C.c_double),
         ("phi_cutoff", C.c_double),
+        ("method", C.c_int),
     ]
 
 
@@ -78,6 +79,9 @@ def lib():
         L.orc_phi.argtypes = [C.c_double, C.c_double]
         L.orc_force_term.argtypes = [C.c_double] * 6 + [dp]
         L.orc_collide_node.argtypes = [C.c_double, dp, C.c_double, C.c_double, C.c_double, dp, dp, dp]
+        L.orc_collide_node_ps.argtypes = [C.c_double, dp, C.c_double, C.c_double, C.c_double, dp, dp, dp]
+        L.orc_cell_fraction.argtypes = [C.c_double, C.c_double, C.c_double]
+        L.orc_cell_fraction.restype = C.c_double
         L.orc_wan_turek.argtypes = [C.POINTER(OrcParams), C.POINTER(OrcParticle), C.c_int, dp]
         L.orc_set_threads.argtypes = [C.c_int]
         L.orc_max_threads.restype = C.c_int
@@ -101,6 +105,7 @@ def make_params(prob, phi_cutoff: float = 0.0) -> OrcParams:
     p.force_model = prob.force_model
     p.eps_p, p.eps_p2, p.eps_w, p.eps_w2, p.xi = prob.wan_turek
     p.phi_cutoff = phi_cutoff
+    p.method = getattr(prob, "method", 0)
     return p
 
 
@@ -210,6 +215,18 @@ def collide_node(tau, f, phi_, usx, usy):
     fo, Fi, mom = np.empty(9), np.empty(9), np.empty(5)
     lib().orc_collide_node(tau, np.ascontiguousarray(f, dtype=np.float64), phi_, usx, usy, fo, Fi, mom)
     return fo, Fi, mom
+
+
+def collide_node_ps(tau, f, B, usx, usy):
+    """PS-LBM collision (Eq. 7 with Omega^s of Eq. 9): (f', Omega^s, (rho, u*x, u*y))."""
+    fo, om, mom = np.empty(9), np.empty(9), np.empty(3)
+    lib().orc_collide_node_ps(tau, np.ascontiguousarray(f, dtype=np.float64), B, usx, usy, fo, om, mom)
+    return fo, om, mom
+
+
+def cell_fraction(dx: float, dy: float, r: float) -> float:
+    """Area of the unit cell centred at (dx, dy) covered by the disc of radius r at the origin."""
+    return float(lib().orc_cell_fraction(dx, dy, r))
 
 
 def wan_turek(prob) -> np.ndarray:

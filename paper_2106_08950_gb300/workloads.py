@@ -32,6 +32,8 @@ PERIODIC = "periodic"
 VELOCITY = "velocity"   # Dirichlet velocity side, density taken from the inner node
 PRESSURE = "pressure"   # Dirichlet density side, velocity taken from the inner node
 
+METHOD_DI = 0           # the diffuse-interface LBM (Eqs. 13-19)
+METHOD_PS = 1           # the partially saturated LBM with the SP collision (Eqs. 7-11)
 FORCE_EQ18 = 0          # hydrodynamic force as printed in Eq. 18
 FORCE_MOMENTUM = 1      # momentum given up by the fluid in the collision
 
@@ -72,6 +74,7 @@ class Problem:
     rho_init: float = 1.0
     u0: Tuple[float, float] = (0.0, 0.0)
     force_model: int = FORCE_EQ18
+    method: int = 0                  # METHOD_DI (the paper's DI-LBM) or METHOD_PS (its PS-LBM comparison)
     # Wan-Turek stiffness (Eqs. 28-29): eps_P, eps_P', eps_W, eps_W', xi
     wan_turek: Tuple[float, float, float, float, float] = (1e30, 1e30, 5e29, 5e29, 1.0)
     particles: List[Particle] = field(default_factory=list)

@@ -421,3 +421,100 @@ def test_settling_velocity_against_eq27():
         v[fm] = -st[0, 4]
     assert 0.6 < v[W.FORCE_MOMENTUM] / u_eq27 < 1.2
     assert abs(v[W.FORCE_EQ18] / v[W.FORCE_MOMENTUM] * (1 - 0.5 / tau) - 1.0) < 0.05
+
+
+# ---------------------------------------------------------------- PS-LBM (Sec. 2.2)
+@pytest.mark.parametrize("r", [0.3, 0.5, 1.0, 2.5, 6.3, 12.9])
+def test_cell_fraction_sums_to_the_disc_area(r):
+    # The cells tile the plane, so the covered fractions of a disc anywhere sum
+    # to pi r^2 (also when the circle touches cell edges).
+    rng = np.random.default_rng(int(r * 100))
+    for cx, cy in list(rng.uniform(-0.5, 0.5, size=(4, 2))) + [(0.0, 0.5 - r % 1.0), (0.5, 0.5)]:
+        n = int(r) + 3
+        tot = sum(O.cell_fraction(x - cx, y - cy, r) for x in range(-n, n + 1) for y in range(-n, n + 1))
+        assert abs(tot - math.pi * r * r) <= 1e-12 * math.pi * r * r, (r, cx, cy, tot)
+
+
+def test_cell_fraction_closed_forms():
+    # cell fully inside / outside; a unit disc with the cell's corner at its
+    # centre covers a quarter disc; a disc of radius 1/2 centred in the cell
+    # lies inside it; a straight boundary (huge r) cuts the cell linearly.
+    assert O.cell_fraction(0.0, 0.0, 5.0) == 1.0
+    assert O.cell_fraction(7.0, 0.0, 5.0) == 0.0
+    assert abs(O.cell_fraction(0.5, 0.5, 1.0) - math.pi / 4) < 1e-14
+    assert abs(O.cell_fraction(0.0, 0.0, 0.5) - math.pi / 4) < 1e-14
+    R = 1e5
+    for t in (-0.4, -0.1, 0.0, 0.25):
+        assert abs(O.cell_fraction(R + t, 0.0, R) - (0.5 - t)) < 1e-5
+    # symmetries of the square and the disc
+    for dx, dy, r in [(3.2, 1.7, 3.9), (-2.3, 4.4, 5.1), (0.4, -6.6, 6.5)]:
+        e = O.cell_fraction(dx, dy, r)
+        for ex in (O.cell_fraction(-dx, dy, r), O.cell_fraction(dx, -dy, r), O.cell_fraction(dy, dx, r)):
+            assert abs(e - ex) < 1e-14
+
+
+def test_cell_fraction_against_sampling():
+    # 1500^2 midpoint samples of boundary cells: sampling error below 2e-4
+    rng = np.random.default_rng(7)
+    g = (np.arange(1500) + 0.5) / 1500 - 0.5
+    X, Y = np.meshgrid(g, g)
+    checked = 0
+    while checked < 12:
+        r = float(rng.uniform(2.5, 12.0))
+        a = float(rng.uniform(0, 2 * math.pi))
+        d = r + float(rng.uniform(-0.7, 0.7))
+        dx, dy = d * math.cos(a), d * math.sin(a)
+        e = O.cell_fraction(dx, dy, r)
+        if not 0.0 < e < 1.0:
+            continue
+        bf = float(np.mean((X + dx) ** 2 + (Y + dy) ** 2 < r * r))
+        assert abs(e - bf) < 2e-4, (dx, dy, r, e, bf)
+        checked += 1
+
+
+@pytest.mark.parametrize("B", [0.0, 0.37, 1.0])
+def test_ps_collision_eq7_eq9_equals_eq12(B):
+    # The paper gives the SP collision twice: Eq. 7 with Omega^s of Eq. 9, and
+    # the single-term form Eq. 12.  They must agree; the collision keeps mass,
+    # hands the fluid B rho (u_s - u*) of momentum, and sum_i Omega^s_i c_i =
+    # rho (u_s - u*), so the force of Eq. 10 is -B rho (u_s - u*).  B = 0 is BGK.
+    tau = 0.8
+    f = O.equilibrium(1.02, 0.02, -0.03) + RNG.uniform(-2e-3, 2e-3, size=9)
+    us = (0.05, -0.01)
+    fo, om, mom = O.collide_node_ps(tau, f, B, *us)
+    rho = f.sum()
+    ua = (C_LAT.T @ f) / rho
+    feq = O.equilibrium(rho, *ua)
+    feqs = O.equilibrium(rho, *us)
+    eq12 = f - (f - feq) / tau + B * (feqs - feq)
+    assert np.allclose(fo, eq12, atol=1e-16)
+    assert abs(fo.sum() - rho) < 1e-15
+    assert np.allclose(C_LAT.T @ (fo - f), B * rho * (np.array(us) - ua), atol=1e-16)
+    assert np.allclose(C_LAT.T @ om, rho * (np.array(us) - ua), atol=1e-16)
+    if B == 0.0:
+        assert np.allclose(fo, f - (f - feq) / tau, atol=1e-16)
+
+
+def test_ps_periodic_box_conserves_mass_and_momentum():
+    # PS-LBM force (Eq. 10) is exactly the momentum the collision hands the
+    # fluid, so with periodic streaming P_fluid + sum m U stays constant, and
+    # the total mass too.
+    prob = _moving_box()
+    prob.method = W.METHOD_PS
+    sim = O.OracleSim(prob)
+    masses = np.array([q.rho_s * math.pi * q.r ** 2 for q in prob.particles])
+
+    def totals():
+        f = sim.populations()
+        pf = np.array([np.einsum("i,iyx->", C_LAT[:, a], f) for a in (0, 1)])
+        _, _, st = sim.forces()
+        return f.sum(), pf + (masses[:, None] * st[:, 3:5]).sum(axis=0)
+
+    sim.step(1)
+    m0, p0 = totals()
+    sim.step(60)
+    m1, p1 = totals()
+    assert abs(m1 - m0) < 1e-10 * m0
+    assert np.allclose(p1, p0, atol=1e-11)
+    phi = sim.fields()[3]
+    assert phi.max() == 1.0 and 0.0 < phi[(phi > 0) & (phi < 1)].min()   # interior and partial cells
