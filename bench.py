@@ -45,6 +45,8 @@ def parse():
     ap.add_argument("--impl", default="dilbm", choices=["dilbm", "reference"])
     ap.add_argument("--workload", default="periodic", choices=["periodic", "sedimentation", "cylinder", "batch", "serve"])
     ap.add_argument("--storage", default="fp32", choices=["fp32", "fp16", "bf16"])
+    ap.add_argument("--method", default="di", choices=["di", "ps"],
+                    help="coupling: the paper's DI-LBM, or its PS-LBM comparison (periodic/cylinder/sedimentation)")
     ap.add_argument("--size", type=int, default=4096, help="periodic box edge")
     ap.add_argument("--particles", type=int, default=2048)
     ap.add_argument("--e2e-steps", type=int, default=200)
@@ -70,6 +72,11 @@ def make_problem(args, rank=0):
     else:
         p = W.cylinder_drag()
         cfg = {"workload": "cylinder drag 200x100, r=10, U=0.05, Re=20, eps=2"}
+    if args.method == "ps":
+        p.method = W.METHOD_PS
+        cfg["method"] = "PS-LBM, SP collision (Eqs. 7-12), exact covered cell fraction"
+    else:
+        cfg["method"] = "DI-LBM (Eqs. 13-19)"
     return p, cfg
 
 
@@ -210,6 +217,7 @@ def reference_arm(args):
     n_small = 512
     count = max(1, round(len(prob.particles) * (n_small / max(prob.nx, 1)) ** 2)) if args.workload == "periodic" else 0
     small = (W.periodic_suspension(n=n_small, count=count, seed=3) if args.workload == "periodic" else prob)
+    small.method = prob.method
     from oracle import oracle as O
     sim = O.OracleSim(small, phi_cutoff=4 * small.eps)
     for _ in range(args.warmup):
@@ -264,6 +272,7 @@ def gpu_arm(args):
 
     import torch
     from paper_2106_08950_gb300 import dilbm as D
+    from paper_2106_08950_gb300 import workloads as W
 
     world, rank, local = dist_env()
     torch.cuda.set_device(local)
@@ -368,7 +377,9 @@ def gpu_arm(args):
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         v, n, dt, cores = oracle_mlups(prob, args.cpu_seconds)
         line["cpu_baseline"] = {"value": v, "unit": "MLUPS", "cores": cores, "kind": "oracle",
-                                "sample": f"{n} steps of the full workload ({dt:.1f} s), phi cutoff 4 widths"}
+                                "sample": f"{n} steps of the full workload ({dt:.1f} s), " + (
+                                    "cell fractions within r + 0.71" if prob.method == W.METHOD_PS
+                                    else "phi cutoff 4 widths")}
     if rank == 0:
         print(json.dumps(line), flush=True)
     sim.close()

@@ -63,6 +63,22 @@ typedef enum {
     DILBM_FORCE_MOMENTUM = 1   /* the momentum the collision hands the fluid, negated */
 } dilbm_force_model;
 
+/*
+ * The fluid-particle coupling.  DILBM_METHOD_DI is the paper's method: the
+ * smooth solid fraction phi of Eq. 14 and the collision of Eqs. 13, 15-17.
+ * DILBM_METHOD_PS is the method the paper compares it with (Sec. 2.2), the
+ * partially saturated LBM with the SP collision: B = eps_s (Eq. 8), the exact
+ * area of each node's unit cell covered by a particle, the collision of
+ * Eq. 12 (f^eq takes the fluid velocity, no correction step) and the force of
+ * Eqs. 10-11.  The interface width is unused by PS.  PS contexts need
+ * particles of radius >= 1, run the sweep in its default shape, and are
+ * stepped on their own (batches, servers and dilbm_step_static take DI only).
+ */
+typedef enum {
+    DILBM_METHOD_DI = 0,
+    DILBM_METHOD_PS = 1
+} dilbm_method;
+
 typedef struct {
     int kind;                  /* dilbm_side_kind */
     double ux, uy;             /* DILBM_SIDE_VELOCITY: boundary velocity */
@@ -79,6 +95,7 @@ typedef struct {
     int storage;               /* dilbm_storage */
     int force_model;           /* dilbm_force_model */
     double wan_turek[5];       /* eps_P, eps_P', eps_W, eps_W', xi of Eqs. 28-29 */
+    int method;                /* dilbm_method (0: DI) */
 } dilbm_grid;
 
 typedef struct {
@@ -234,7 +251,9 @@ int dilbm_batch_set_shape(dilbm_batch *batch, int warps, int blocks_per_sm);
  * per process, keyed by storage, edge handling and lattice size (for a
  * batch: storage, member count and total row segments), so tuning a second
  * context or batch of the same key launches nothing.  Both synchronise.
- * dilbm_set_shape / dilbm_batch_set_shape set a shape by hand.
+ * dilbm_set_shape / dilbm_batch_set_shape set a shape by hand.  A PS-LBM
+ * context keeps the default shape (8 warps, blocks_per_sm 0): dilbm_autotune
+ * reports it without timing and dilbm_set_shape rejects any other.
  * Errors: INVALID_ARG, CUDA.
  */
 int dilbm_autotune(dilbm_ctx *ctx, int reps, int *warps, int *blocks_per_sm);

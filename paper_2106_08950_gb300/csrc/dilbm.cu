@@ -43,6 +43,7 @@ struct dilbm_ctx {
     Physics ph{};
     BodyParams bp{};
     int storage = DILBM_FP32;
+    int method = DILBM_METHOD_DI;
     size_t elem = 4;
     void *buf[2] = {nullptr, nullptr};
     int cur = 0;
@@ -219,17 +220,23 @@ SweepArgs<T> sweep_args(const dilbm_ctx *c, int cur, const void *src, void *dst,
 }
 
 // The FIELDS-mode sweep (dilbm_fields) in the default shape.
-template <typename T, bool EDGES>
-cudaError_t launch_fields_sweep(dilbm_ctx *c, const void *src, FieldsOut fo) {
+template <typename T, bool EDGES, bool PS>
+cudaError_t launch_fields_sweep_m(dilbm_ctx *c, const void *src, FieldsOut fo) {
     static int cache[64] = {};
     constexpr size_t smem = sweep_smem_bytes<T>();
     int per_sm = 1;
-    cudaError_t e = occupancy_of(sweep_kernel<T, MODE_FIELDS, EDGES>, SWEEP_WARPS, smem, cache, &per_sm);
+    cudaError_t e = occupancy_of(sweep_kernel<T, MODE_FIELDS, EDGES, SWEEP_WARPS, PS>, SWEEP_WARPS, smem, cache, &per_sm);
     if (e != cudaSuccess) return e;
     const long long blocks = persistent_grid((long long)c->L.ny * c->L.ntx, SWEEP_WARPS, per_sm, c->num_sms, SweepShape{});
-    sweep_kernel<T, MODE_FIELDS, EDGES><<<(unsigned)blocks, SWEEP_WARPS * 32, smem, c->stream>>>(
+    sweep_kernel<T, MODE_FIELDS, EDGES, SWEEP_WARPS, PS><<<(unsigned)blocks, SWEEP_WARPS * 32, smem, c->stream>>>(
         sweep_args<T>(c, c->cur, src, nullptr, false, fo));
     return cudaGetLastError();
+}
+
+template <typename T, bool EDGES>
+cudaError_t launch_fields_sweep(dilbm_ctx *c, const void *src, FieldsOut fo) {
+    return c->method == DILBM_METHOD_PS ? launch_fields_sweep_m<T, EDGES, true>(c, src, fo)
+                                        : launch_fields_sweep_m<T, EDGES, false>(c, src, fo);
 }
 
 bool has_edges(const dilbm_ctx *c) { return !(c->L.per_x && c->L.per_y); }
@@ -239,6 +246,23 @@ cudaError_t step_sweep(dilbm_ctx *c, const SweepShape &sh, bool query = false, i
     const void *src = c->buf[c->cur];
     void *dst = c->buf[c->cur ^ 1];
     const bool edges = has_edges(c);
+    if (c->method == DILBM_METHOD_PS) {       // the comparison method: default shape only
+        if (query) {
+            if (per_sm) *per_sm = 1;
+            return cudaSuccess;
+        }
+        switch (c->storage) {
+        case DILBM_FP32:
+            return launch_step_sweep_ps<float>(sweep_args<float>(c, c->cur, src, dst, true, FieldsOut{}), edges,
+                                               c->num_sms, c->stream);
+        case DILBM_FP16_DEV:
+            return launch_step_sweep_ps<__half>(sweep_args<__half>(c, c->cur, src, dst, true, FieldsOut{}), edges,
+                                                c->num_sms, c->stream);
+        default:
+            return launch_step_sweep_ps<__nv_bfloat16>(
+                sweep_args<__nv_bfloat16>(c, c->cur, src, dst, true, FieldsOut{}), edges, c->num_sms, c->stream);
+        }
+    }
     switch (c->storage) {
     case DILBM_FP32:
         return launch_step_sweep<float>(sweep_args<float>(c, c->cur, src, dst, true, FieldsOut{}), edges, sh,
@@ -366,6 +390,13 @@ namespace dilbm {
 // Lets other translation units of the library report through dilbm_last_error().
 int set_last_error(int code, const std::string &msg) { return fail(code, msg); }
 
+// Distance beyond a particle's surface at which its coupling vanishes: the
+// phi tail (DI) or the half-diagonal of a cell (PS: a cell whose centre is
+// farther than r + sqrt(2)/2 has no covered part).
+double reach_cut(int method, double interface_width) {
+    return method == DILBM_METHOD_PS ? 0.70711 : PHI_CUT_WIDTHS * interface_width;
+}
+
 // Every argument check of dilbm_create (host only; g must not be NULL).
 int check_problem(const dilbm_grid *g, dilbm_lattice lattice, double tau, double interface_width,
                   const dilbm_particle *particles, int np) {
@@ -389,7 +420,14 @@ int check_problem(const dilbm_grid *g, dilbm_lattice lattice, double tau, double
     for (int k = 0; k < 5; ++k)
         if (!(g->wan_turek[k] > 0.0)) return fail(DILBM_ERR_INVALID_ARG, "Wan-Turek parameters must be > 0");
     if ((rc = check_particles(g, particles, np))) return rc;
-    return check_reach(PHI_CUT_WIDTHS * interface_width, particles, np);
+    if (g->method != DILBM_METHOD_DI && g->method != DILBM_METHOD_PS)
+        return fail(DILBM_ERR_INVALID_ARG, "unknown coupling method");
+    if (g->method == DILBM_METHOD_PS) {
+        for (int k = 0; k < np; ++k)
+            if (!(particles[k].r >= 1.0))
+                return fail(DILBM_ERR_INVALID_ARG, "PS-LBM particles need a radius >= 1 lattice unit");
+    }
+    return check_reach(reach_cut(g->method, interface_width), particles, np);
 }
 }  // namespace dilbm
 
@@ -408,6 +446,7 @@ int dilbm_create(const dilbm_grid *g, dilbm_lattice lattice, double tau, double 
     c->stream = (cudaStream_t)cuda_stream;
     c->np = np;
     c->storage = g->storage;
+    c->method = g->method;
     c->elem = g->storage == DILBM_FP32 ? 4 : 2;
     Lattice &L = c->L;
     L.nx = g->nx;
@@ -447,8 +486,14 @@ int dilbm_create(const dilbm_grid *g, dilbm_lattice lattice, double tau, double 
     ph.kf = (float)(1.0 - 0.5 / tau);
     ph.kforce = g->force_model == DILBM_FORCE_EQ18 ? ph.kf : 1.0f;
     ph.four_over_eps = (float)(4.0 / interface_width);
-    ph.cut_d = PHI_CUT_WIDTHS * interface_width;
+    ph.cut_d = dilbm::reach_cut(g->method, interface_width);
     ph.cut = (float)ph.cut_d;
+    if (c->method == DILBM_METHOD_PS) {
+        // Eq. 12: the second moment's coupling term is B rho (u_s u_s - u* u*)
+        // and the force of Eq. 10 is the momentum the fluid receives
+        ph.kf = 1.0f;
+        ph.kforce = 1.0f;
+    }
     BodyParams &bp = c->bp;
     bp.np = np;
     bp.gx = g->gravity[0];
@@ -902,6 +947,8 @@ int dilbm_batch_create(dilbm_ctx *const *members, int n, void *cuda_stream, dilb
         if (!members[k]) return fail(DILBM_ERR_INVALID_ARG, "NULL member context");
         if (members[k]->storage != members[0]->storage)
             return fail(DILBM_ERR_INVALID_ARG, "all members of a batch must use the same storage");
+        if (members[k]->method != DILBM_METHOD_DI)
+            return fail(DILBM_ERR_INVALID_ARG, "batches advance DI-LBM contexts only");
         for (int j = 0; j < k; ++j)
             if (members[j] == members[k]) return fail(DILBM_ERR_INVALID_ARG, "a context appears twice in the batch");
     }
@@ -1160,6 +1207,8 @@ extern "C" {
 int dilbm_set_shape(dilbm_ctx *c, int warps, int blocks_per_sm) {
     const SweepShape sh{warps, blocks_per_sm};
     if (!c || !shape_valid(sh)) return fail(DILBM_ERR_INVALID_ARG, "warps must be 2, 4 or 8 and blocks_per_sm >= 0");
+    if (c->method == DILBM_METHOD_PS && !same_shape(sh, SweepShape{}))
+        return fail(DILBM_ERR_INVALID_ARG, "a PS-LBM context runs the sweep in the default shape (8 warps, 0)");
     if (!same_shape(sh, c->shape)) {
         DILBM_CUDA(cudaStreamSynchronize(c->stream));
         drop_graphs(c);
@@ -1171,6 +1220,10 @@ int dilbm_set_shape(dilbm_ctx *c, int warps, int blocks_per_sm) {
 int dilbm_autotune(dilbm_ctx *c, int reps, int *warps, int *blocks_per_sm) {
     if (!c) return fail(DILBM_ERR_INVALID_ARG, "NULL context");
     if (reps <= 0) reps = 10;
+    if (c->method == DILBM_METHOD_PS) {         // one shape only: nothing to time
+        report_shape(c->shape, warps, blocks_per_sm);
+        return DILBM_OK;
+    }
     const auto key = std::make_tuple(0, c->storage, has_edges(c) ? 1 : 0, (long long)c->L.nx, (long long)c->L.ny);
     SweepShape best = c->shape;
     if (!tuned(key, &best)) {

@@ -470,6 +470,130 @@ __device__ __noinline__ Pop9 edge_values(const T *__restrict__ src, const Lattic
     return out;
 }
 
+// ------------------------------------------------------------ PS-LBM solid fraction
+// The paper's comparison method (PS-LBM, Sec. 2.2) weights its collision by
+// B = eps_s (Eq. 8), the area of the node's unit cell covered by the solid.
+// cell_cover returns the area of [dx - 1/2, dx + 1/2] x [dy - 1/2, dy + 1/2]
+// inside the disc of radius r >= 1 centred at the origin: the shoelace area
+// of the polygon formed, counter-clockwise, by the corners inside the disc
+// and the points where the circle crosses the cell edges, plus the circular
+// segment between each chord that polygon draws across the circle and its
+// arc.  The polygon is summed in the cell's own frame (coordinates of size
+// 1/2, so FP32 keeps ~1e-6).  Each corner is classified once (inside:
+// distance < r) and every edge takes its crossings from the classes of its
+// two ends (one crossing where they differ; none or two where both are
+// outside), so a corner on the circle, seen by two edges, cannot be counted
+// twice or lost.  For r >= 1 every arc inside a unit cell is a minor arc.
+__device__ __forceinline__ float segment_area(float ex, float ey, float ix, float iy, float r, float rinv) {
+    // area between the chord E-I and the minor arc: r^2 (asin s - s sqrt(1 - s^2)), s = |EI| / 2r
+    const float s = 0.5f * sqrtf((ix - ex) * (ix - ex) + (iy - ey) * (iy - ey)) * rinv;
+    float g;
+    if (s < 0.3f) {     // Taylor series: 2/3 s^3 + 1/5 s^5 + 3/28 s^7 + 5/72 s^9 + 35/704 s^11
+        const float s2 = s * s;
+        g = s * s2 * (2.0f / 3.0f + s2 * (0.2f + s2 * (3.0f / 28.0f + s2 * (5.0f / 72.0f + s2 * (35.0f / 704.0f)))));
+    } else {
+        g = asinf(s) - s * sqrtf((1.0f - s) * (1.0f + s));
+    }
+    return r * r * g;
+}
+
+// The polygon and segment sums of cell_cover, fed one boundary point at a
+// time in counter-clockwise order.
+struct CoverWalk {
+    float r, rinv;
+    float area2 = 0.f, seg = 0.f;
+    float fx = 0.f, fy = 0.f, lx = 0.f, ly = 0.f;   // first and last polygon vertex
+    float ex = 0.f, ey = 0.f, ix0 = 0.f, iy0 = 0.f; // pending exit; first entry seen before any exit
+    bool any = false, pending = false, first_entry = false;
+
+    __device__ __forceinline__ void vertex(float vx, float vy) {
+        if (any) area2 += lx * vy - vx * ly;
+        else { fx = vx; fy = vy; any = true; }
+        lx = vx; ly = vy;
+    }
+    __device__ __forceinline__ void entry(float vx, float vy) {
+        if (pending) { seg += segment_area(ex, ey, vx, vy, r, rinv); pending = false; }
+        else if (!first_entry) { first_entry = true; ix0 = vx; iy0 = vy; }
+        vertex(vx, vy);
+    }
+    __device__ __forceinline__ void exit(float vx, float vy) {
+        vertex(vx, vy);
+        ex = vx; ey = vy; pending = true;
+    }
+};
+
+// Half the chord the circle cuts on a line at distance |p| from the centre.
+__device__ __forceinline__ float half_chord(float p, float r) {
+    const float a = fabsf(p);
+    return sqrtf(fmaxf((r - a) * (r + a), 0.f));
+}
+
+__device__ __forceinline__ float clampf(float v, float lo, float hi) { return fminf(fmaxf(v, lo), hi); }
+
+static __device__ __noinline__ float cell_cover(float dx, float dy, float r) {
+    // the cell's extent about the disc centre; corners 0..3 counter-clockwise
+    // from (x0, y0), edge k from corner k to corner k + 1
+    const float x0 = dx - 0.5f, x1 = dx + 0.5f, y0 = dy - 0.5f, y1 = dy + 0.5f;
+    const float r2 = r * r;
+    const float xx0 = x0 * x0, xx1 = x1 * x1, yy0 = y0 * y0, yy1 = y1 * y1;
+    const bool in0 = xx0 + yy0 < r2, in1 = xx1 + yy0 < r2, in2 = xx1 + yy1 < r2, in3 = xx0 + yy1 < r2;
+    // both ends outside: the circle crosses twice iff the foot of the
+    // perpendicular from the centre lies inside the edge and |p| < r
+    const bool mx = x0 < 0.f && 0.f < x1, my = y0 < 0.f && 0.f < y1;
+    CoverWalk w;
+    w.r = r;
+    w.rinv = __frcp_rn(r);
+
+    // edge 0: y = y0, x rising; enters at x = -h, leaves at x = +h
+    if (in0) w.vertex(-0.5f, -0.5f);
+    {
+        const bool two = !in0 && !in1 && mx && fabsf(y0) < r;
+        const bool en = !in0 && (in1 || two), ex = !in1 && (in0 || two);
+        if (en || ex) {
+            const float h = half_chord(y0, r);
+            if (en) w.entry(clampf(-h, x0, x1) - dx, -0.5f);
+            if (ex) w.exit(clampf(h, x0, x1) - dx, -0.5f);
+        }
+    }
+    // edge 1: x = x1, y rising; enters at y = -h, leaves at y = +h
+    if (in1) w.vertex(0.5f, -0.5f);
+    {
+        const bool two = !in1 && !in2 && my && fabsf(x1) < r;
+        const bool en = !in1 && (in2 || two), ex = !in2 && (in1 || two);
+        if (en || ex) {
+            const float h = half_chord(x1, r);
+            if (en) w.entry(0.5f, clampf(-h, y0, y1) - dy);
+            if (ex) w.exit(0.5f, clampf(h, y0, y1) - dy);
+        }
+    }
+    // edge 2: y = y1, x falling; enters at x = +h, leaves at x = -h
+    if (in2) w.vertex(0.5f, 0.5f);
+    {
+        const bool two = !in2 && !in3 && mx && fabsf(y1) < r;
+        const bool en = !in2 && (in3 || two), ex = !in3 && (in2 || two);
+        if (en || ex) {
+            const float h = half_chord(y1, r);
+            if (en) w.entry(clampf(h, x0, x1) - dx, 0.5f);
+            if (ex) w.exit(clampf(-h, x0, x1) - dx, 0.5f);
+        }
+    }
+    // edge 3: x = x0, y falling; enters at y = +h, leaves at y = -h
+    if (in3) w.vertex(-0.5f, 0.5f);
+    {
+        const bool two = !in3 && !in0 && my && fabsf(x0) < r;
+        const bool en = !in3 && (in0 || two), ex = !in0 && (in3 || two);
+        if (en || ex) {
+            const float h = half_chord(x0, r);
+            if (en) w.entry(-0.5f, clampf(h, y0, y1) - dy);
+            if (ex) w.exit(-0.5f, clampf(-h, y0, y1) - dy);
+        }
+    }
+    if (!w.any) return 0.f;
+    w.area2 += w.lx * w.fy - w.fx * w.ly;
+    if (w.pending && w.first_entry) w.seg += segment_area(w.ex, w.ey, w.ix0, w.iy0, r, w.rinv);
+    return 0.5f * w.area2 + w.seg;
+}
+
 // ------------------------------------------------------------ the sweep
 // Mode: STEP writes the collided populations and the force partials; FIELDS
 // writes rho, the corrected velocity and phi of the streamed state instead.
@@ -538,7 +662,7 @@ struct Ring {
 // hand the stage to the segment `nxt` (row ny2, segment nx2 of lattice An)
 // when there is one, then stream, collide, store and sum the segment's
 // force / torque.  Returns false if the bounded wait gave up.
-template <typename T, int MODE, bool EDGES>
+template <typename T, int MODE, bool EDGES, bool PS = false>
 __device__ __forceinline__ bool sweep_segment(const SweepArgs<T> &A, int y, int tx, T *stage, Ring &ring, int s,
                                               bool has_next, const SweepArgs<T> &An, int ny2, int nx2,
                                               float4 *crec, int *cid, int lane) {
@@ -676,8 +800,15 @@ __device__ __forceinline__ bool sweep_segment(const SweepArgs<T> &A, int y, int 
             if (d2 > R * R) continue;
             const float l = rb.x - sqrtf(d2);
             if (l < -ph.cut) continue;
-            // (1 + tanh(2l/eps)) / 2 == 1 / (1 + exp(-4l/eps))
-            const float pc = __frcp_rn(1.0f + expf(-ph.four_over_eps * l));
+            float pc;
+            if constexpr (PS) {
+                // covered cell fraction (B = eps_s, Eq. 8): 1 once every corner is inside
+                pc = l >= ph.cut ? 1.0f : cell_cover(dx, dy, rb.x);
+                if (!(pc > 0.f)) continue;
+            } else {
+                // (1 + tanh(2l/eps)) / 2 == 1 / (1 + exp(-4l/eps))
+                pc = __frcp_rn(1.0f + expf(-ph.four_over_eps * l));
+            }
             if (pc > phi[q] || (pc == phi[q] && pc > 0.f && id < best_id[q])) {
                 phi[q] = pc; best[q] = c; best_id[q] = id; rxn[q] = dx; ryn[q] = dy;
             }
@@ -768,7 +899,8 @@ __device__ __forceinline__ bool sweep_segment(const SweepArgs<T> &A, int y, int 
             const float2 usx = add2(ua, dux), usy = add2(va, duy);
             const float2 phq = make_float2(phi[qa], phi[qb]);
             // ---- corrected velocity (Eq. 17)
-            const float2 hph = mul2(f2(0.5f), phq);
+            // (PS-LBM: f^eq takes the fluid velocity u*, there is no correction)
+            const float2 hph = mul2(f2(PS ? 0.0f : 0.5f), phq);
             const float2 ux = fma2(hph, dux, ua), uy = fma2(hph, duy, va);
 
             if (MODE == MODE_FIELDS) {
@@ -896,7 +1028,7 @@ struct SweepSmem {
 // round-robin (neighbouring warps on neighbouring segments); each warp keeps
 // STAGES segments staged ahead.  W warps per block (rows in flight per
 // block); every W caps registers at 128 per thread.
-template <typename T, int MODE, bool EDGES, int W = SWEEP_WARPS>
+template <typename T, int MODE, bool EDGES, int W = SWEEP_WARPS, bool PS = false>
 __global__ void __launch_bounds__(W * 32, 16 / W)
 sweep_kernel(const __grid_constant__ SweepArgs<T> one)
 {
@@ -952,7 +1084,7 @@ sweep_kernel(const __grid_constant__ SweepArgs<T> one)
         }
         const int s = k % STAGES;
         const bool has_next = item + STAGES * nw < nitems;
-        if (!sweep_segment<T, MODE, EDGES>(one, y, tx, sm.stages + s * stage_elems<T>(), ring, s, has_next, one, ay, atx,
+        if (!sweep_segment<T, MODE, EDGES, PS>(one, y, tx, sm.stages + s * stage_elems<T>(), ring, s, has_next, one, ay, atx,
                                            sm.crec, sm.cid, lane)) {
             timed_out = true;
             break;

@@ -87,6 +87,19 @@ cudaError_t batch_variant(const BatchArgs<T> &ba, const SweepShape &sh, int num_
     return cudaGetLastError();
 }
 
+// The PS-LBM step sweep (the paper's comparison method), in the default shape.
+template <typename T, bool EDGES>
+cudaError_t ps_variant(const SweepArgs<T> &a, int num_sms, cudaStream_t st) {
+    static int cache[64] = {};
+    constexpr size_t smem = sweep_smem_bytes<T>();
+    int per_sm = 1;
+    cudaError_t e = occupancy_of(sweep_kernel<T, MODE_STEP, EDGES, SWEEP_WARPS, true>, SWEEP_WARPS, smem, cache, &per_sm);
+    if (e != cudaSuccess) return e;
+    const long long blocks = persistent_grid((long long)a.L.ny * a.L.ntx, SWEEP_WARPS, per_sm, num_sms, SweepShape{});
+    sweep_kernel<T, MODE_STEP, EDGES, SWEEP_WARPS, true><<<(unsigned)blocks, SWEEP_WARPS * 32, smem, st>>>(a);
+    return cudaGetLastError();
+}
+
 // Generic bodies of the per-storage launchers.
 template <typename T>
 cudaError_t step_sweep_impl(const SweepArgs<T> &a, bool edges, const SweepShape &sh, int num_sms, cudaStream_t st,
@@ -126,6 +139,11 @@ cudaError_t launch_batch_sweep(const BatchArgs<T> &ba, const SweepShape &sh, int
 template <> cudaError_t launch_step_sweep<float>(const SweepArgs<float> &, bool, const SweepShape &, int, cudaStream_t, bool, int *);
 template <> cudaError_t launch_step_sweep<__half>(const SweepArgs<__half> &, bool, const SweepShape &, int, cudaStream_t, bool, int *);
 template <> cudaError_t launch_step_sweep<__nv_bfloat16>(const SweepArgs<__nv_bfloat16> &, bool, const SweepShape &, int, cudaStream_t, bool, int *);
+template <typename T>
+cudaError_t launch_step_sweep_ps(const SweepArgs<T> &a, bool edges, int num_sms, cudaStream_t st);
+template <> cudaError_t launch_step_sweep_ps<float>(const SweepArgs<float> &, bool, int, cudaStream_t);
+template <> cudaError_t launch_step_sweep_ps<__half>(const SweepArgs<__half> &, bool, int, cudaStream_t);
+template <> cudaError_t launch_step_sweep_ps<__nv_bfloat16>(const SweepArgs<__nv_bfloat16> &, bool, int, cudaStream_t);
 template <> cudaError_t launch_batch_sweep<float>(const BatchArgs<float> &, const SweepShape &, int, cudaStream_t, bool, int *);
 template <> cudaError_t launch_batch_sweep<__half>(const BatchArgs<__half> &, const SweepShape &, int, cudaStream_t, bool, int *);
 template <> cudaError_t launch_batch_sweep<__nv_bfloat16>(const BatchArgs<__nv_bfloat16> &, const SweepShape &, int, cudaStream_t, bool, int *);

@@ -17,4 +17,9 @@ cudaError_t launch_batch_sweep<__nv_bfloat16>(const BatchArgs<__nv_bfloat16> &ba
     return batch_sweep_impl<__nv_bfloat16>(ba, sh, num_sms, st, query, per_sm);
 }
 
+template <>
+cudaError_t launch_step_sweep_ps<__nv_bfloat16>(const SweepArgs<__nv_bfloat16> &a, bool edges, int num_sms, cudaStream_t st) {
+    return edges ? ps_variant<__nv_bfloat16, true>(a, num_sms, st) : ps_variant<__nv_bfloat16, false>(a, num_sms, st);
+}
+
 }  // namespace dilbm

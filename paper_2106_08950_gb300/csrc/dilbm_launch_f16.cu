@@ -17,4 +17,9 @@ cudaError_t launch_batch_sweep<__half>(const BatchArgs<__half> &ba, const SweepS
     return batch_sweep_impl<__half>(ba, sh, num_sms, st, query, per_sm);
 }
 
+template <>
+cudaError_t launch_step_sweep_ps<__half>(const SweepArgs<__half> &a, bool edges, int num_sms, cudaStream_t st) {
+    return edges ? ps_variant<__half, true>(a, num_sms, st) : ps_variant<__half, false>(a, num_sms, st);
+}
+
 }  // namespace dilbm

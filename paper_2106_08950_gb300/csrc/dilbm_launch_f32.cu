@@ -17,4 +17,9 @@ cudaError_t launch_batch_sweep<float>(const BatchArgs<float> &ba, const SweepSha
     return batch_sweep_impl<float>(ba, sh, num_sms, st, query, per_sm);
 }
 
+template <>
+cudaError_t launch_step_sweep_ps<float>(const SweepArgs<float> &a, bool edges, int num_sms, cudaStream_t st) {
+    return edges ? ps_variant<float, true>(a, num_sms, st) : ps_variant<float, false>(a, num_sms, st);
+}
+
 }  // namespace dilbm

@@ -205,6 +205,7 @@ int dilbm_server_submit(dilbm_server *s, const dilbm_job *job, long long *id) {
     g.storage = s->cfg.storage;
     int rc = dilbm::check_problem(&g, DILBM_D2Q9, job->tau, job->interface_width, job->particles, job->np);
     if (rc) return rc;
+    if (g.method != DILBM_METHOD_DI) return sfail(DILBM_ERR_INVALID_ARG, "the server runs DI-LBM jobs only");
     unsigned long long fp = 0;
     if ((rc = dilbm_footprint(&g, job->np, &fp))) return rc;
     if (fp > s->budget)

@@ -125,6 +125,7 @@ extern "C" int dilbm_step_static(const dilbm_grid *g, double tau, double interfa
         return sfail(DILBM_ERR_INVALID_ARG, "dilbm_step_static: an axis must be periodic on both sides or neither");
     if (g->force_model != DILBM_FORCE_EQ18 && g->force_model != DILBM_FORCE_MOMENTUM)
         return sfail(DILBM_ERR_INVALID_ARG, "dilbm_step_static: unknown force model");
+    if (g->method != DILBM_METHOD_DI) return sfail(DILBM_ERR_INVALID_ARG, "dilbm_step_static: DI-LBM only");
     if (!(g->rho_f > 0.0)) return sfail(DILBM_ERR_INVALID_ARG, "dilbm_step_static: rho_f must be > 0");
     for (int k = 0; k < 5; ++k)
         if (!(g->wan_turek[k] > 0.0)) return sfail(DILBM_ERR_INVALID_ARG, "dilbm_step_static: Wan-Turek parameters must be > 0");

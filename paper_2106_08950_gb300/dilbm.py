@@ -46,7 +46,7 @@ class Grid(C.Structure):
                 ("west", Side), ("east", Side), ("south", Side), ("north", Side),
                 ("gravity", C.c_double * 2), ("rho_f", C.c_double), ("rho_init", C.c_double),
                 ("u0", C.c_double * 2), ("storage", C.c_int), ("force_model", C.c_int),
-                ("wan_turek", C.c_double * 5)]
+                ("wan_turek", C.c_double * 5), ("method", C.c_int)]
 
 
 class Particle(C.Structure):
@@ -177,6 +177,7 @@ def make_grid(prob: W.Problem, storage: str = "fp32") -> Grid:
     g.force_model = prob.force_model
     for k in range(5):
         g.wan_turek[k] = prob.wan_turek[k]
+    g.method = getattr(prob, "method", W.METHOD_DI)
     return g
 
 

@@ -46,7 +46,7 @@ def test_struct_sizes_match_header_layout():
     # dilbm_side: int + 3 doubles (with padding) = 32 bytes; dilbm_particle: 8 doubles + int.
     assert C.sizeof(D.Side) == 32
     assert C.sizeof(D.Particle) == 72
-    assert C.sizeof(D.Grid) == 8 + 4 * 32 + 16 + 8 + 8 + 16 + 8 + 40
+    assert C.sizeof(D.Grid) == 8 + 4 * 32 + 16 + 8 + 8 + 16 + 8 + 40 + 8   # ... wan_turek, method (+ padding)
 
 
 def _create(lib, prob, tau=None, eps=None, lattice=0, storage="fp32"):
