@@ -354,7 +354,7 @@ def gpu_arm(args):
     per_launch_ms = sweep_ms / max(sweep_n, 1)
     alg_bytes = BYTES_PER_NODE[args.storage] * nodes
     achieved = alg_bytes / (per_launch_ms / 1e3) / 1e9
-    traffic = measured_traffic(f"{args.workload}:{args.storage}:{prob.nx}x{prob.ny}")
+    traffic = measured_traffic(f"{args.workload}:{args.storage}:{prob.nx}x{prob.ny}" + (":ps" if prob.method == W.METHOD_PS else ""))
     roof = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
             "traffic": traffic, "peak_kind": peak_kind,
             "kernel": "sweep_kernel", "sweep_ms_per_launch": per_launch_ms,
