@@ -50,6 +50,20 @@
  *   8'. force and torque by the double sums of Eqs. 10-11.
  * The same max rule picks a node's owner (the largest covered fraction).
  *
+ * Moving computational domain (Sec. 3.5, after Wang et al. 2013): the paper
+ * moves the domain one lattice unit whenever the tracked particle has moved
+ * one lattice unit, and gives no further detail.  Reading: at the end of a
+ * step, with d the tracked particle's x at the start of that step minus the
+ * reference x_ref (minimum image on a periodic x axis), the frame moves by
+ * s = +1 column if d >= 1, by -1 if d <= -1, else not at all.  Moving by s
+ * takes the post-collision populations of column x + s to column x (on a
+ * periodic axis the columns roll; otherwise the entering column repeats its
+ * neighbour, a zero-gradient state that the edge scheme then overwrites),
+ * subtracts s from every particle's new x and adds s to the frame offset.
+ * The move is plain: in a pressure-driven channel it displaces the linear
+ * pressure field by one column against the fixed end densities (a step of
+ * (rho_in - rho_out) / (nx - 1)), which the ends re-absorb acoustically.
+ *
  * Memory layout: populations f[i][y][x], x fastest, i = 0..8 in the order of
  * Eq. 3: (0,0) (1,0) (0,1) (-1,0) (0,-1) (1,1) (-1,1) (-1,-1) (1,-1).
  */
@@ -107,6 +121,9 @@ typedef struct {
     double *force;      /* np x 3: Fx, Fy, T of the last step */
     double *fcol;       /* np x 2: Wan-Turek force of the last step */
     long long steps;
+    int track;          /* moving frame: tracked particle, -1 when off */
+    double track_x;     /* its reference x in the frame */
+    long long offset;   /* columns the frame has moved (x_lab = x + offset) */
 } orc_sim;
 
 /* ---------------------------------------------------------------- helpers */
@@ -355,12 +372,24 @@ orc_sim *orc_create(const orc_params *p, const orc_particle *parts, int np)
     s->gy = (double *)malloc(sizeof(double) * n);
     s->force = (double *)calloc(3 * (np > 0 ? np : 1), sizeof(double));
     s->fcol = (double *)calloc(2 * (np > 0 ? np : 1), sizeof(double));
+    s->track = -1;
     double feq[9];
     orc_equilibrium(p->rho_init, p->u0x, p->u0y, feq);
     for (int i = 0; i < 9; ++i)
         for (size_t k = 0; k < n; ++k) s->f[i * n + k] = feq[i];
     return s;
 }
+
+/* Moving frame (Sec. 3.5): track `particle` (-1: off) about x_ref. */
+int orc_set_moving_frame(orc_sim *s, int particle, double x_ref)
+{
+    if (particle < -1 || particle >= s->np || !isfinite(x_ref)) return -1;
+    s->track = particle;
+    s->track_x = x_ref;
+    return 0;
+}
+
+long long orc_frame_offset(const orc_sim *s) { return s->offset; }
 
 void orc_destroy(orc_sim *s)
 {
@@ -560,8 +589,41 @@ static void stream_and_boundaries(orc_sim *s)
     }
 }
 
-/* Steps 8-9: force/torque sums and the rigid-body update. */
-static void particles_update(orc_sim *s)
+/* The frame's move at the end of this step, from the tracked particle's x
+ * at its start. */
+static int frame_shift(const orc_sim *s)
+{
+    if (s->track < 0) return 0;
+    double d = s->parts[s->track].x - s->track_x;
+    if (periodic_x(&s->p)) d = min_image(d, s->p.nx);
+    return d >= 1.0 ? 1 : (d <= -1.0 ? -1 : 0);
+}
+
+/* Column x takes the post-collision populations of column x + sh. */
+static void shift_populations(orc_sim *s, int sh)
+{
+    const orc_params *p = &s->p;
+    int nx = p->nx, ny = p->ny;
+    size_t n = (size_t)nx * ny;
+    double *row = (double *)malloc(sizeof(double) * nx);
+    for (int i = 0; i < 9; ++i) {
+        for (int y = 0; y < ny; ++y) {
+            double *f = s->f + i * n + (size_t)y * nx;
+            memcpy(row, f, sizeof(double) * nx);
+            for (int x = 0; x < nx; ++x) {
+                int src = x + sh;
+                if (periodic_x(p)) src = (src % nx + nx) % nx;
+                else src = src < 0 ? 0 : (src > nx - 1 ? nx - 1 : src);
+                f[x] = row[src];
+            }
+        }
+    }
+    free(row);
+}
+
+/* Steps 8-9: force/torque sums and the rigid-body update; then the frame
+ * moves by sh columns. */
+static void particles_update(orc_sim *s, int sh)
 {
     const orc_params *p = &s->p;
     int nx = p->nx, ny = p->ny;
@@ -593,6 +655,15 @@ static void particles_update(orc_sim *s)
         P->theta += P->omega;
         if (periodic_x(p)) { P->x = fmod(P->x, (double)nx); if (P->x < 0.0) P->x += nx; }
         if (periodic_y(p)) { P->y = fmod(P->y, (double)ny); if (P->y < 0.0) P->y += ny; }
+    }
+    if (sh) {
+        for (int q = 0; q < s->np; ++q) {
+            orc_particle *P = &s->parts[q];
+            P->x -= sh;
+            if (periodic_x(p)) { P->x = fmod(P->x, (double)nx); if (P->x < 0.0) P->x += nx; }
+        }
+        shift_populations(s, sh);
+        s->offset += sh;
     }
 }
 
@@ -646,7 +717,7 @@ int orc_step(orc_sim *s, long long nsteps)
                 for (int i = 0; i < 9; ++i) s->f[i * n + k] = fo[i];
             }
         }
-        particles_update(s);
+        particles_update(s, frame_shift(s));
         s->steps++;
         if (bad) return -4;
     }

@@ -87,6 +87,10 @@ def lib():
         L.orc_max_threads.restype = C.c_int
         L.orc_steps_done.restype = C.c_longlong
         L.orc_steps_done.argtypes = [C.c_void_p]
+        L.orc_set_moving_frame.restype = C.c_int
+        L.orc_set_moving_frame.argtypes = [C.c_void_p, C.c_int, C.c_double]
+        L.orc_frame_offset.restype = C.c_longlong
+        L.orc_frame_offset.argtypes = [C.c_void_p]
         _lib = L
     return _lib
 
@@ -162,6 +166,16 @@ class OracleSim:
     @property
     def steps_done(self) -> int:
         return int(self.L.orc_steps_done(self.h))
+
+    def set_moving_frame(self, particle: int, x_ref: float) -> None:
+        """Moving computational domain (Sec. 3.5): the frame follows particle
+        ``particle`` (-1: off) about ``x_ref``, one column at a time."""
+        if self.L.orc_set_moving_frame(self.h, int(particle), float(x_ref)) != 0:
+            raise ValueError("bad moving-frame particle or reference")
+
+    def frame_offset(self) -> int:
+        """Columns the frame has moved: lab x = frame x + offset."""
+        return int(self.L.orc_frame_offset(self.h))
 
     def fields(self):
         """rho, ux, uy, phi as (ny, nx) float64 and the owner map (int32)."""
