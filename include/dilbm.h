@@ -159,6 +159,35 @@ int dilbm_force_mean(dilbm_ctx *ctx, double *mean, long long *nsteps);
 int dilbm_force_mean_reset(dilbm_ctx *ctx);
 
 /*
+ * Moving computational domain (Sec. 3.5: the domain moves one lattice unit
+ * whenever the particle has moved one, after Wang et al. 2013).  From the
+ * next step on, the frame follows particle `particle` (0 <= particle < np;
+ * -1 switches the frame off) about the reference x_ref: at the end of each
+ * step, with d the particle's x at the start of that step minus x_ref
+ * (minimum image on a periodic x axis), the frame moves s = +1 column when
+ * d >= 1, s = -1 when d <= -1, else not at all.  Moving by s takes the
+ * populations of column x + s to column x (rolled on a periodic x axis;
+ * otherwise the entering column repeats its neighbour, a zero-gradient state
+ * the edge scheme then overwrites), subtracts s from every particle's x and
+ * adds s to the frame offset: lab x = frame x + offset.  The move is plain:
+ * in a pressure-driven channel it displaces the linear pressure field by
+ * one column against the fixed end densities, which the ends re-absorb.
+ * Positions reported by dilbm_forces() are frame positions.  One more
+ * kernel launch per step while the frame is on.  Requires
+ * nx x (bytes per stored population) <= 48 KiB.  Contexts with a moving
+ * frame cannot join a batch.
+ * Errors: INVALID_ARG (particle out of range, x_ref not finite, lattice too
+ * wide), CUDA.
+ */
+int dilbm_set_moving_frame(dilbm_ctx *ctx, int particle, double x_ref);
+
+/*
+ * Columns the frame has moved since create (0 if it never moved).  offset:
+ * host.  Synchronises the stream.  Errors: INVALID_ARG, CUDA.
+ */
+int dilbm_frame_offset(dilbm_ctx *ctx, long long *offset);
+
+/*
  * Macroscopic fields at the current time level, row-major [ny][nx] FP32:
  * density (Eq. 5), corrected velocity (Eq. 17) and solid fraction (Eq. 14),
  * taken from the populations the next step would collide.  Any pointer may be

@@ -67,6 +67,9 @@ struct dilbm_ctx {
     long long launches = 0;
     SweepShape shape{};               // launch shape of the step sweep (autotuned or default)
     cudaGraphExec_t g_pair[2] = {nullptr, nullptr};   // two steps from parity 0 / 1, replayed by dilbm_step
+    int track = -1;                   // moving frame: tracked particle, -1 when off
+    double track_x = 0.0;             // its reference x
+    long long *frame_off = nullptr;   // device: columns the frame has moved, allocated on first use
     void *owned[32] = {};
     int nowned = 0;
 };
@@ -163,6 +166,8 @@ PartArgs particle_args(const dilbm_ctx *c, int cur, int integrate) {
     a.fcol = c->fcol;
     a.fsum = integrate ? c->fsum : nullptr;
     a.err = c->err;
+    a.track = c->track;
+    a.track_x = c->track_x;
     return a;
 }
 
@@ -176,6 +181,35 @@ int launch_particles(dilbm_ctx *c, int integrate) {
 }
 
 void drop_graphs(dilbm_ctx *c);
+
+// Rows of shared memory the moving frame's in-place column shift may use.
+constexpr size_t FRAME_ROW_BYTES = 48 * 1024;
+
+// The moving frame's column shift of the populations the next step reads,
+// decided from the tracked particle's position at the start of this step.
+int launch_frame_shift(dilbm_ctx *c) {
+    const int blocks = c->L.ny < 2 * c->num_sms ? c->L.ny : 2 * c->num_sms;
+    const size_t smem = (size_t)c->L.nx * c->elem;
+    void *dst = c->buf[c->cur ^ 1];
+    const double *xt = c->P.x[c->cur];
+    switch (c->storage) {
+    case DILBM_FP32:
+        frame_shift_kernel<float><<<blocks, 256, smem, c->stream>>>((float *)dst, c->L, xt, c->track, c->track_x,
+                                                                    c->frame_off);
+        break;
+    case DILBM_FP16_DEV:
+        frame_shift_kernel<__half><<<blocks, 256, smem, c->stream>>>((__half *)dst, c->L, xt, c->track, c->track_x,
+                                                                     c->frame_off);
+        break;
+    default:
+        frame_shift_kernel<__nv_bfloat16><<<blocks, 256, smem, c->stream>>>((__nv_bfloat16 *)dst, c->L, xt, c->track,
+                                                                            c->track_x, c->frame_off);
+        break;
+    }
+    DILBM_CUDA(cudaGetLastError());
+    c->launches += 1;
+    return DILBM_OK;
+}
 
 int upload_particles(dilbm_ctx *c, const dilbm_particle *p, int np) {
     const int wx = c->L.wrap_x, wy = c->L.wrap_y;
@@ -315,6 +349,7 @@ int one_step(dilbm_ctx *c) {
     if (rc) return rc;
     if (c->timing) DILBM_CUDA(cudaEventRecord(e1, c->stream));
     if (c->np > 0 && (rc = launch_particles(c, 1))) return rc;
+    if (c->track >= 0 && (rc = launch_frame_shift(c))) return rc;
     c->cur ^= 1;
     c->fsum_steps += 1;
     return DILBM_OK;
@@ -636,6 +671,34 @@ int dilbm_force_mean(dilbm_ctx *c, double *mean, long long *nsteps) {
     return rc;
 }
 
+int dilbm_set_moving_frame(dilbm_ctx *c, int particle, double x_ref) {
+    if (!c) return fail(DILBM_ERR_INVALID_ARG, "NULL context");
+    if (particle < -1 || particle >= c->np)
+        return fail(DILBM_ERR_INVALID_ARG, "moving frame: particle index out of range");
+    if (particle >= 0 && !std::isfinite(x_ref)) return fail(DILBM_ERR_INVALID_ARG, "moving frame: x_ref not finite");
+    if (particle >= 0 && (size_t)c->L.nx * c->elem > FRAME_ROW_BYTES)
+        return fail(DILBM_ERR_INVALID_ARG, "moving frame: a row of nx populations exceeds " +
+                                               std::to_string(FRAME_ROW_BYTES) + " bytes");
+    if (!c->frame_off) {
+        int rc = dev_alloc(c, &c->frame_off, 1);
+        if (rc) return rc;
+        DILBM_CUDA(cudaMemsetAsync(c->frame_off, 0, sizeof(long long), c->stream));
+    }
+    c->track = particle;
+    c->track_x = particle >= 0 ? x_ref : 0.0;
+    drop_graphs(c);
+    return DILBM_OK;
+}
+
+int dilbm_frame_offset(dilbm_ctx *c, long long *offset) {
+    if (!c || !offset) return fail(DILBM_ERR_INVALID_ARG, "NULL argument");
+    *offset = 0;
+    if (!c->frame_off) return DILBM_OK;
+    DILBM_CUDA(cudaMemcpyAsync(offset, c->frame_off, sizeof(long long), cudaMemcpyDeviceToHost, c->stream));
+    DILBM_CUDA(cudaStreamSynchronize(c->stream));
+    return DILBM_OK;
+}
+
 int dilbm_force_mean_reset(dilbm_ctx *c) {
     if (!c) return fail(DILBM_ERR_INVALID_ARG, "NULL context");
     if (c->np > 0) DILBM_CUDA(cudaMemsetAsync(c->fsum, 0, sizeof(double) * 3 * c->np, c->stream));
@@ -949,6 +1012,8 @@ int dilbm_batch_create(dilbm_ctx *const *members, int n, void *cuda_stream, dilb
             return fail(DILBM_ERR_INVALID_ARG, "all members of a batch must use the same storage");
         if (members[k]->method != DILBM_METHOD_DI)
             return fail(DILBM_ERR_INVALID_ARG, "batches advance DI-LBM contexts only");
+        if (members[k]->track >= 0)
+            return fail(DILBM_ERR_INVALID_ARG, "batches advance fixed-frame contexts only");
         for (int j = 0; j < k; ++j)
             if (members[j] == members[k]) return fail(DILBM_ERR_INVALID_ARG, "a context appears twice in the batch");
     }

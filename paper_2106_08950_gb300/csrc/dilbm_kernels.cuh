@@ -1225,7 +1225,22 @@ struct PartArgs {
     double *force, *fcol;
     double *fsum;               // nullable: running sum of (Fx, Fy, T) over integrating steps
     int *err;
+    int track;                  // moving frame: tracked particle, -1 when off
+    double track_x;             // its reference x
 };
+
+// Moving computational domain (Sec. 3.5): the frame's move at the end of a
+// step, in columns, from the tracked particle's x at the start of that step
+// (minimum image on a periodic x axis): +1 once it is one lattice unit or
+// more ahead of the reference, -1 once one or more behind.
+__host__ __device__ inline int frame_move(double xt, double xref, int nx, int per_x) {
+    double d = xt - xref;
+    if (per_x) {
+        while (d >= 0.5 * nx) d -= nx;
+        while (d < -0.5 * nx) d += nx;
+    }
+    return d >= 1.0 ? 1 : (d <= -1.0 ? -1 : 0);
+}
 
 __device__ __forceinline__ void particle_body(const PartArgs &A, int p, int lane) {
     const Lattice &L = A.L;
@@ -1364,6 +1379,15 @@ __device__ __forceinline__ void particle_body(const PartArgs &A, int p, int lane
             }
         }
     }
+    if (integrate && A.track >= 0) {
+        // the frame moves with the tracked particle: every particle, fixed
+        // ones included, shifts by the same whole number of columns
+        const int s = frame_move(xin[A.track], A.track_x, L.nx, L.per_x);
+        if (s) {
+            nX -= (double)s;
+            if (L.per_x) { nX = fmod(nX, (double)L.nx); if (nX < 0.0) nX += L.nx; }
+        }
+    }
     if (lane == 0) {
         xout[p] = nX; yout[p] = nY;
         xfout[p] = (float)nX; yfout[p] = (float)nY;
@@ -1472,6 +1496,37 @@ __global__ void import_kernel(T *__restrict__ dst, Lattice L, const double *__re
 }
 
 // Uniform initial state f^eq(rho0, u0) written as deviations on every node.
+// Moving computational domain (Sec. 3.5): when the frame moves by s columns
+// (decided from the tracked particle's x at the start of the step that just
+// ran, as the particle update decided it), column x of every population
+// plane takes the stored values of column x + s: rolled on a periodic x
+// axis, otherwise clamped, so the entering column repeats its neighbour.
+// The move is in place, one row of one plane at a time through shared
+// memory (nx elements); block 0 adds s to the frame offset.
+template <typename T>
+__global__ void frame_shift_kernel(T *__restrict__ buf, Lattice L, const double *__restrict__ xt, int track,
+                                   double track_x, long long *__restrict__ offset) {
+    extern __shared__ __align__(16) unsigned char frame_row[];
+    T *row = reinterpret_cast<T *>(frame_row);
+    const int s = frame_move(xt[track], track_x, L.nx, L.per_x);
+    if (s == 0) return;
+    if (blockIdx.x == 0 && threadIdx.x == 0) *offset += s;
+    for (int y = blockIdx.x; y < L.ny; y += gridDim.x) {
+        for (int i = 0; i < 9; ++i) {
+            T *line = buf + (long long)i * L.plane + (long long)y * L.pitch;
+            for (int x = threadIdx.x; x < L.nx; x += blockDim.x) row[x] = line[x];
+            __syncthreads();
+            for (int x = threadIdx.x; x < L.nx; x += blockDim.x) {
+                int src = x + s;
+                if (L.per_x) src = src < 0 ? src + L.nx : (src >= L.nx ? src - L.nx : src);
+                else src = src < 0 ? 0 : (src > L.nx - 1 ? L.nx - 1 : src);
+                line[x] = row[src];
+            }
+            __syncthreads();
+        }
+    }
+}
+
 template <typename T>
 __global__ void init_kernel(T *__restrict__ dst, Lattice L, float drho, float ux, float uy) {
     const long long n = (long long)L.nx * L.ny;

@@ -139,6 +139,8 @@ def load_library(path: Optional[str] = None):
     L.dilbm_server_result.argtypes = [vp, C.c_longlong, vp, vp, vp]
     L.dilbm_force_mean.argtypes = [vp, vp, C.POINTER(C.c_longlong)]
     L.dilbm_force_mean_reset.argtypes = [vp]
+    L.dilbm_set_moving_frame.argtypes = [vp, C.c_int, C.c_double]
+    L.dilbm_frame_offset.argtypes = [vp, C.POINTER(C.c_longlong)]
     L.dilbm_server_clock.argtypes = [vp]
     L.dilbm_server_clock.restype = C.c_double
     L.dilbm_server_destroy.argtypes = [vp]
@@ -149,7 +151,8 @@ def load_library(path: Optional[str] = None):
                  "dilbm_batch_set_timing", "dilbm_batch_sweep_time", "dilbm_batch_errors", "dilbm_footprint",
                  "dilbm_server_create", "dilbm_server_submit", "dilbm_server_progress", "dilbm_server_status",
                  "dilbm_server_result", "dilbm_force_mean", "dilbm_force_mean_reset", "dilbm_autotune",
-                 "dilbm_set_shape", "dilbm_batch_autotune", "dilbm_batch_set_shape"):
+                 "dilbm_set_shape", "dilbm_batch_autotune", "dilbm_batch_set_shape", "dilbm_set_moving_frame",
+                 "dilbm_frame_offset"):
         getattr(L, name).restype = C.c_int
     if path == LIB_PATH:
         _lib = L
@@ -277,6 +280,19 @@ class Simulation:
 
     def force_mean_reset(self) -> None:
         check(self.L.dilbm_force_mean_reset(self.h))
+
+    def set_moving_frame(self, particle: int, x_ref: float = None) -> None:
+        """Moving computational domain (Sec. 3.5): the frame follows particle
+        ``particle`` (-1: off) about ``x_ref`` (default: its initial x)."""
+        if x_ref is None:
+            x_ref = self.prob.particles[particle].x if particle >= 0 else 0.0
+        check(self.L.dilbm_set_moving_frame(self.h, int(particle), float(x_ref)))
+
+    def frame_offset(self) -> int:
+        """Columns the frame has moved: lab x = frame x + offset."""
+        k = C.c_longlong()
+        check(self.L.dilbm_frame_offset(self.h, C.byref(k)))
+        return int(k.value)
 
     def forces_into(self, F: np.ndarray) -> None:
         """Copy Fx, Fy, T of the last step into a host array of np x 3 doubles."""
