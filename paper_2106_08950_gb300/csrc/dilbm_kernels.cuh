@@ -484,7 +484,9 @@ __device__ __noinline__ Pop9 edge_values(const T *__restrict__ src, const Lattic
 // two ends (one crossing where they differ; none or two where both are
 // outside), so a corner on the circle, seen by two edges, cannot be counted
 // twice or lost.  For r >= 1 every arc inside a unit cell is a minor arc.
-__device__ __forceinline__ float segment_area(float ex, float ey, float ix, float iy, float r, float rinv) {
+// Both routines stay out of line: inlined into the sweep's four node slots
+// they evict the sweep's own code from the instruction cache.
+static __device__ __noinline__ float segment_area(float ex, float ey, float ix, float iy, float r, float rinv) {
     // area between the chord E-I and the minor arc: r^2 (asin s - s sqrt(1 - s^2)), s = |EI| / 2r
     const float s = 0.5f * sqrtf((ix - ex) * (ix - ex) + (iy - ey) * (iy - ey)) * rinv;
     float g;
