@@ -84,3 +84,44 @@ def test_random_lattice_matches_oracle(stream, seed):
         ok, e = PAR.compare_state(Sg, So)
         assert ok, (prob.name, e)
     g.close()
+
+
+def ps_frame_case(seed):
+    """The same random lattices with the comparison method (two in three) and,
+    in two of three cases with discs, a frame that follows the first disc
+    about a reference 1 to 2 lattice units from its start, so the frame moves
+    at least once, often on consecutive steps."""
+    prob, steps = random_case(seed)
+    rng = np.random.default_rng(5000 + seed)
+    if seed % 3 != 2:
+        prob.method = W.METHOD_PS
+    x_ref = None
+    if prob.particles and seed % 3 != 1:
+        x_ref = prob.particles[0].x + float(rng.choice([-1.0, 1.0]) * rng.uniform(1.0, 2.0))
+    return prob, steps, x_ref
+
+
+@pytest.mark.parametrize("seed", range(40, 70))
+def test_random_lattice_ps_or_moving_frame_matches_oracle(stream, seed):
+    prob, steps, x_ref = ps_frame_case(seed)
+    g = D.Simulation(prob, stream=stream)
+    o = O.OracleSim(prob)
+    if x_ref is not None:
+        g.set_moving_frame(0, x_ref)
+        o.set_moving_frame(0, x_ref)
+    g.step(steps)
+    o.step(steps)
+    g.sync()
+    assert g.frame_offset() == o.frame_offset()
+    fo = o.fields()
+    ok, errs = PAR.compare_fields(g.fields(), fo)
+    assert ok, (prob.name, prob.method, x_ref, errs)
+    if prob.particles:
+        Fg, _, Sg = g.forces()
+        Fo, _, So = o.forces()
+        atol = PAR.ps_force_floor(fo[3], So) if prob.method == W.METHOD_PS else 0.0
+        ok, e = PAR.compare_forces(Fg, Fo, PAR.TOL_FP32_SUSPENSION_FORCE, max(q.r for q in prob.particles), atol=atol)
+        assert ok, (prob.name, prob.method, x_ref, e)
+        ok, e = PAR.compare_state(Sg, So)
+        assert ok, (prob.name, prob.method, x_ref, e)
+    g.close()
