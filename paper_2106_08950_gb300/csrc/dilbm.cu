@@ -70,6 +70,7 @@ struct dilbm_ctx {
     int track = -1;                   // moving frame: tracked particle, -1 when off
     double track_x = 0.0;             // its reference x
     long long *frame_off = nullptr;   // device: columns the frame has moved, allocated on first use
+    float *cover = nullptr;           // PS: per-particle covered-area tables (grown by upload_particles)
     void *owned[32] = {};
     int nowned = 0;
 };
@@ -177,6 +178,14 @@ int launch_particles(dilbm_ctx *c, int integrate) {
                                                                           nullptr, BatchIndex{});
     DILBM_CUDA(cudaGetLastError());
     c->launches += 1;
+    if (c->method == DILBM_METHOD_PS) {
+        // the covered-area tables of the positions just written
+        const int pout = integrate ? c->cur ^ 1 : c->cur;
+        cover_kernel<<<np, dim3(COVER_BX, COVER_BY), 0, c->stream>>>(c->cover, c->P.x[pout], c->P.y[pout], c->P.r, np,
+                                                                     c->ph);
+        DILBM_CUDA(cudaGetLastError());
+        c->launches += 1;
+    }
     return DILBM_OK;
 }
 
@@ -211,12 +220,35 @@ int launch_frame_shift(dilbm_ctx *c) {
     return DILBM_OK;
 }
 
+// PS-LBM: each particle's table of covered cell areas spans the cells within
+// K = ceil(r_max + reach) + 1 of its centre cell; grown when a larger radius
+// arrives (the particles kernel fills it, the sweep reads it).
+int size_cover_tables(dilbm_ctx *c, const dilbm_particle *p, int np) {
+    if (c->method != DILBM_METHOD_PS || np == 0) return DILBM_OK;
+    double rmax = 0.0;
+    for (int k = 0; k < np; ++k) rmax = p[k].r > rmax ? p[k].r : rmax;
+    const int K = (int)std::ceil(rmax + c->ph.cut_d) + 1;
+    if (K <= c->ph.ck) return DILBM_OK;
+    const size_t S = 2 * (size_t)K + 1;
+    if (c->cover) {
+        DILBM_CUDA(cudaStreamSynchronize(c->stream));
+        DILBM_CUDA(cudaFree(c->cover));
+        c->cover = nullptr;
+    }
+    DILBM_CUDA(cudaMalloc(&c->cover, sizeof(float) * S * S * (size_t)np));
+    c->ph.ck = K;
+    c->bins[0].cover = c->bins[1].cover = c->cover;
+    drop_graphs(c);
+    return DILBM_OK;
+}
+
 int upload_particles(dilbm_ctx *c, const dilbm_particle *p, int np) {
     const int wx = c->L.wrap_x, wy = c->L.wrap_y;
     set_wrap_flags(c, p, np);
     if (c->L.wrap_x != wx || c->L.wrap_y != wy) drop_graphs(c);
     int rc = check_reach(c->ph.cut_d, p, np);
     if (rc) return rc;
+    if ((rc = size_cover_tables(c, p, np))) return rc;
     std::vector<double> h(8 * (size_t)np);
     std::vector<int> fx(np);
     for (int k = 0; k < np; ++k) {
@@ -618,7 +650,7 @@ int dilbm_step(dilbm_ctx *c, long long nsteps) {
         int rc = capture_pair(c, c->cur);
         if (rc) return rc;
         for (; t + 2 <= nsteps; t += 2) DILBM_CUDA(cudaGraphLaunch(c->g_pair[c->cur], c->stream));
-        c->launches += t * (c->np > 0 ? 2 : 1);
+        c->launches += t * ((c->np > 0 ? (c->method == DILBM_METHOD_PS ? 3 : 2) : 1) + (c->track >= 0 ? 1 : 0));
         c->fsum_steps += t;
     }
     for (; t < nsteps; ++t) {
@@ -790,6 +822,7 @@ void dilbm_destroy(dilbm_ctx *c) {
     cudaStreamSynchronize(c->stream);
     drop_graphs(c);
     for (int k = 0; k < c->nowned; ++k) cudaFree(c->owned[k]);
+    if (c->cover) cudaFree(c->cover);
     for (cudaEvent_t e : c->ev) cudaEventDestroy(e);
     delete c;
 }

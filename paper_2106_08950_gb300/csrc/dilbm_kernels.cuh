@@ -184,6 +184,7 @@ struct Physics {
     float kforce;               // kf (Eq. 18 as printed) or 1 (momentum exchange)
     float four_over_eps;        // 4 / epsilon: phi = 1 / (1 + exp(-4 l / eps))
     float cut;                  // phi tail kept while l >= -cut
+    int ck;                     // PS: half-width K of each particle's covered-area table (0: none)
     double cut_d;
 };
 
@@ -191,9 +192,12 @@ struct Bins {                   // one set per step parity
     int *count;                 // per tile: particles binned (may exceed MAXC)
     int *ids;                   // per tile: MAXC particle ids
     float4 *rec;                // per tile and slot, 3 records: (cx_hi, cx_lo, cy_hi, cy_lo),
-                                // (r, ux_hi, uy_hi, omega_hi), (ux_lo, uy_lo, omega_lo, 0)
+                                // (r, ux_hi, uy_hi, omega_hi), (ux_lo, uy_lo, omega_lo, packed
+                                // floor(cx), floor(cy): 16 bits each)
     int *pslot;                 // per particle: MAXT entries tile * MAXC + slot (-1: overflowed)
     int *npslot;                // per particle: tiles reached
+    float *cover;               // PS: per particle, the covered areas of the (2K+1)^2 cells about
+                                // (floor X, floor Y), row-major; shared by both parities
 };
 
 // ------------------------------------------------------------ small helpers
@@ -784,7 +788,16 @@ __device__ __forceinline__ bool sweep_segment(const SweepArgs<T> &A, int y, int 
         // short periodic axes: the stored image may lie several periods away
         // (it is the one nearest the tile centre), so reduce by the nearest
         // multiple of the period (exact: an integer multiple of an integer)
-        if (L.wrap_y) dy = fmaf(-(float)L.ny, rintf(dy * __frcp_rn((float)L.ny)), dy);
+        int ky = 0;                                     // PS: periods removed, for the table index
+        if constexpr (PS) {
+            if (L.wrap_y) {
+                const float k = rintf(dy * __frcp_rn((float)L.ny));
+                dy = fmaf(-(float)L.ny, k, dy);
+                ky = (int)k;
+            }
+        } else {
+            if (L.wrap_y) dy = fmaf(-(float)L.ny, rintf(dy * __frcp_rn((float)L.ny)), dy);
+        }
         const float h2 = R * R - dy * dy;
         if (h2 < 0.f) continue;                         // this row misses the disc tail
         const float dx0 = ((float)(x0 - tx0) - ra.x) - ra.y;
@@ -794,18 +807,38 @@ __device__ __forceinline__ bool sweep_segment(const SweepArgs<T> &A, int y, int 
             if (lo * lo > h2) continue;
         }
         const int id = cid[c];
+        // PS: the centre's whole-cell offsets from the tile origin, packed in the record
+        const int fpk = PS ? __float_as_int(crec[2 * MAXC + c].w) : 0;
 #pragma unroll
         for (int q = 0; q < VEC; ++q) {
             float dx = dx0 + (float)q;
-            if (L.wrap_x) dx = fmaf(-(float)L.nx, rintf(dx * __frcp_rn((float)L.nx)), dx);
+            int kx = 0;
+            if constexpr (PS) {
+                if (L.wrap_x) {
+                    const float k = rintf(dx * __frcp_rn((float)L.nx));
+                    dx = fmaf(-(float)L.nx, k, dx);
+                    kx = (int)k;
+                }
+            } else {
+                if (L.wrap_x) dx = fmaf(-(float)L.nx, rintf(dx * __frcp_rn((float)L.nx)), dx);
+            }
             const float d2 = dx * dx + dy * dy;
             if (d2 > R * R) continue;
             const float l = rb.x - sqrtf(d2);
             if (l < -ph.cut) continue;
             float pc;
             if constexpr (PS) {
-                // covered cell fraction (B = eps_s, Eq. 8): 1 once every corner is inside
-                pc = l >= ph.cut ? 1.0f : cell_cover(dx, dy, rb.x);
+                // covered cell fraction (B = eps_s, Eq. 8): 1 once every corner is
+                // inside, else the particle's table entry for this cell
+                if (l >= ph.cut) {
+                    pc = 1.0f;
+                } else {
+                    const int K = ph.ck, S = 2 * K + 1;
+                    const int ix = lane * VEC + q - (int)(short)(fpk & 0xffff) - L.nx * kx + K;
+                    const int iy = (y - ty0) - (int)(short)((unsigned)fpk >> 16) - L.ny * ky + K;
+                    pc = ((unsigned)ix < (unsigned)S && (unsigned)iy < (unsigned)S)
+                             ? __ldg(A.B.cover + (long long)id * S * S + iy * S + ix) : 0.f;
+                }
                 if (!(pc > 0.f)) continue;
             } else {
                 // (1 + tanh(2l/eps)) / 2 == 1 / (1 + exp(-4l/eps))
@@ -1399,8 +1432,9 @@ __device__ __forceinline__ void particle_body(const PartArgs &A, int p, int lane
     // velocities as FP32 hi + lo: the sweep forms u_s - u*, a small difference
     const float uxh = (float)ux, uyh = (float)uy, omh = (float)om;
     const float4 rb = make_float4((float)r, uxh, uyh, omh);
-    const float4 rl = make_float4((float)(ux - (double)uxh), (float)(uy - (double)uyh), (float)(om - (double)omh), 0.f);
+    const float rlx = (float)(ux - (double)uxh), rly = (float)(uy - (double)uyh), rlz = (float)(om - (double)omh);
     const double R = r + ph.cut_d;
+
     const AxisTiles ax = axis_tiles(nX, R, L.nx, TILE_W, L.ntx, L.per_x);
     const AxisTiles ay = axis_tiles(nY, R, L.ny, TILE_H, L.nty, L.per_y);
     const int NX = range_len(ax), NY = range_len(ay);
@@ -1431,7 +1465,10 @@ __device__ __forceinline__ void particle_body(const PartArgs &A, int p, int lane
             bin_out.ids[entry] = p;
             bin_out.rec[NREC * (long long)entry] = make_float4(cxh, (float)(cx - (double)cxh), cyh, (float)(cy - (double)cyh));
             bin_out.rec[NREC * (long long)entry + 1] = rb;
-            bin_out.rec[NREC * (long long)entry + 2] = rl;
+            // the centre's whole-cell offsets from the tile origin (the PS sweep's table index)
+            const int fxi = (int)floor(cx), fyi = (int)floor(cy);
+            bin_out.rec[NREC * (long long)entry + 2] =
+                make_float4(rlx, rly, rlz, __int_as_float((fxi & 0xffff) | (int)((unsigned)fyi << 16)));
         } else {
             atomicOr(err, ERR_OVERFLOW);
         }
@@ -1498,6 +1535,73 @@ __global__ void import_kernel(T *__restrict__ dst, Lattice L, const double *__re
 }
 
 // Uniform initial state f^eq(rho0, u0) written as deviations on every node.
+// PS-LBM (Sec. 2.2): the covered area of every cell about each particle
+// (B = eps_s, Eq. 8), once per step after the particle update, for the next
+// sweep to look up.  Particle p's table holds the (2K+1)^2 cells about
+// (floor X, floor Y), row-major; the cell at offset (i, j) is the node
+// (floor X + i, floor Y + j).  The same decisions as the sweep's: 0 beyond
+// the reach r + cut, 1 once every corner is inside.  One block per particle
+// walks its table; the particle's fractional centre is formed once in FP64
+// and shared as FP32 hi + lo.  The cells the circle crosses (about one in
+// eight, scattered over every warp) are gathered first and then summed by
+// whole warps; cells past the list's capacity (only for very large discs)
+// are summed where they are found.
+constexpr int COVER_BX = 32, COVER_BY = 8, COVER_RING = 2048;
+
+static __global__ void __launch_bounds__(COVER_BX * COVER_BY)
+cover_kernel(float *__restrict__ cover, const double *__restrict__ xs, const double *__restrict__ ys,
+             const double *__restrict__ rs, int np, Physics ph) {
+    __shared__ int ring[COVER_RING];
+    __shared__ int nring;
+    __shared__ float frac[5];               // x - floor x (hi, lo), y - floor y (hi, lo), r
+    const int tid = threadIdx.y * COVER_BX + threadIdx.x;
+    const int K = ph.ck, S = 2 * K + 1;
+    for (int p = blockIdx.x; p < np; p += gridDim.x) {
+        if (tid == 0) {
+            nring = 0;
+            const double X = xs[p], Y = ys[p];
+            const double fx = X - floor(X), fy = Y - floor(Y);
+            frac[0] = (float)fx;
+            frac[1] = (float)(fx - (double)frac[0]);
+            frac[2] = (float)fy;
+            frac[3] = (float)(fy - (double)frac[2]);
+            frac[4] = (float)rs[p];
+        }
+        __syncthreads();
+        const float rf = frac[4], Rf = rf + ph.cut;
+        float *tab = cover + (long long)p * S * S;
+        for (int iy = threadIdx.y; iy < S; iy += COVER_BY) {
+            const float dy = ((float)(iy - K) - frac[2]) - frac[3];
+            for (int ix = threadIdx.x; ix < S; ix += COVER_BX) {
+                const float dx = ((float)(ix - K) - frac[0]) - frac[1];
+                const float d2 = dx * dx + dy * dy;
+                float v = 0.f;
+                bool crossed = false;
+                if (d2 <= Rf * Rf) {
+                    const float l = rf - sqrtf(d2);
+                    if (l >= ph.cut) v = 1.0f;
+                    else crossed = l >= -ph.cut;
+                }
+                if (crossed) {
+                    const int slot = atomicAdd(&nring, 1);
+                    if (slot < COVER_RING) ring[slot] = iy * S + ix;
+                    else tab[iy * S + ix] = cell_cover(dx, dy, rf);
+                } else {
+                    tab[iy * S + ix] = v;
+                }
+            }
+        }
+        __syncthreads();
+        const int nr = nring < COVER_RING ? nring : COVER_RING;
+        for (int k = tid; k < nr; k += COVER_BX * COVER_BY) {
+            const int j = ring[k], cy = j / S, cx = j - cy * S;
+            const float dx = ((float)(cx - K) - frac[0]) - frac[1], dy = ((float)(cy - K) - frac[2]) - frac[3];
+            tab[j] = cell_cover(dx, dy, rf);
+        }
+        __syncthreads();
+    }
+}
+
 // Moving computational domain (Sec. 3.5): when the frame moves by s columns
 // (decided from the tracked particle's x at the start of the step that just
 // ran, as the particle update decided it), column x of every population

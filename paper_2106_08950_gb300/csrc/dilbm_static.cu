@@ -178,7 +178,7 @@ extern "C" int dilbm_step_static(const dilbm_grid *g, double tau, double interfa
     unsigned char *s = nullptr;
     int rc = scratch_address(&s);
     if (rc) return rc;
-    Bins bins[2];
+    Bins bins[2]{};
     for (int b = 0; b < 2; ++b) {
         bins[b].count = reinterpret_cast<int *>(s + OFF_COUNT) + b * S_MAX_TILES;
         bins[b].ids = reinterpret_cast<int *>(s + OFF_IDS) + (size_t)b * S_MAX_TILES * MAXC;
