@@ -70,9 +70,13 @@ typedef enum {
  * partially saturated LBM with the SP collision: B = eps_s (Eq. 8), the exact
  * area of each node's unit cell covered by a particle, the collision of
  * Eq. 12 (f^eq takes the fluid velocity, no correction step) and the force of
- * Eqs. 10-11.  The interface width is unused by PS.  PS contexts need
- * particles of radius >= 1, run the sweep in its default shape, and are
- * stepped on their own (batches, servers and dilbm_step_static take DI only).
+ * Eqs. 10-11.  The interface width is unused by PS.  Each step one more
+ * kernel tabulates, for every particle, the covered areas of the
+ * (2K+1)^2 cells about its centre cell (K = ceil(r_max + 0.7071) + 1, grown
+ * when dilbm_set_particles brings a larger radius); the sweep looks them up.
+ * PS contexts need particles of radius >= 1, run the sweep in its default
+ * shape, and are stepped on their own (batches, servers and
+ * dilbm_step_static take DI only).
  */
 typedef enum {
     DILBM_METHOD_DI = 0,
@@ -292,7 +296,9 @@ int dilbm_set_shape(dilbm_ctx *ctx, int warps, int blocks_per_sm);
  * Device memory dilbm_create allocates for a lattice of grid->nx x grid->ny
  * with np particles in grid->storage (populations A and B, tile bins, force
  * partials, particle state).  The driver rounds each allocation up, so the
- * memory actually taken is slightly larger.  Host-only arithmetic.
+ * memory actually taken is slightly larger.  A PS context adds its covered-area
+ * tables, np x (2K+1)^2 x 4 bytes, which depend on the radii and are not
+ * counted here.  Host-only arithmetic.
  * Errors: INVALID_ARG (NULL pointer, bad size or storage).
  */
 int dilbm_footprint(const dilbm_grid *grid, int np, unsigned long long *bytes);
