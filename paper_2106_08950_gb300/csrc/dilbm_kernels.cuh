@@ -1260,8 +1260,8 @@ struct PartArgs {
     double *force, *fcol;
     double *fsum;               // nullable: running sum of (Fx, Fy, T) over integrating steps
     int *err;
-    int track;                  // moving frame: tracked particle, -1 when off
-    double track_x;             // its reference x
+    int track = -1;             // moving frame: tracked particle, -1 (the default) when off
+    double track_x = 0.0;       // its reference x
 };
 
 // Moving computational domain (Sec. 3.5): the frame's move at the end of a
