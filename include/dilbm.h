@@ -176,8 +176,10 @@ int dilbm_force_mean_reset(dilbm_ctx *ctx);
  * adds s to the frame offset: lab x = frame x + offset.  The move is plain:
  * in a pressure-driven channel it displaces the linear pressure field by
  * one column against the fixed end densities, which the ends re-absorb.
- * Positions reported by dilbm_forces() are frame positions.  One more
- * kernel launch per step while the frame is on.  Requires
+ * Positions reported by dilbm_forces() are frame positions.  A checkpoint
+ * (dilbm_get_populations, dilbm_forces' state) holds frame positions and
+ * populations: keep the offset beside it.  One more kernel launch per step
+ * while the frame is on.  Requires
  * nx x (bytes per stored population) <= 48 KiB.  Contexts with a moving
  * frame cannot join a batch.
  * Errors: INVALID_ARG (particle out of range, x_ref not finite, lattice too

@@ -125,6 +125,34 @@ def test_ps_solid_fraction_is_the_covered_area(stream):
     assert abs(phig.sum() - phio.sum()) < 1e-3
 
 
+def test_ps_larger_discs_arrive_mid_run(stream):
+    # the per-particle tables of covered areas grow when set_particles brings
+    # a larger radius (and the step graphs are re-captured): the run goes on
+    # matching the oracle, which takes the same particles
+    prob = ps(W.Problem(nx=96, ny=64, tau=0.75, eps=2.0, u0=(0.02, 0.005),
+                        particles=[W.Particle(30.3, 30.7, 3.0, ux=0.01, rho_s=1.4),
+                                   W.Particle(70.6, 25.2, 2.0, uy=0.01, rho_s=1.2)]))
+    g = D.Simulation(prob, stream=stream)
+    o = O.OracleSim(prob)
+    g.step(40)
+    o.step(40)
+    bigger = [W.Particle(30.6, 30.9, 11.5, ux=0.01, rho_s=1.4), W.Particle(71.2, 25.4, 8.25, uy=0.01, rho_s=1.2)]
+    g.set_particles(bigger)
+    o.set_particles(bigger)
+    g.step(60)
+    o.step(60)
+    fo = o.fields()
+    ok, errs = PAR.compare_fields(g.fields(), fo)
+    assert ok, errs
+    assert np.abs(g.fields()[3] - fo[3]).max() < 5e-6
+    Fg, _, Sg = g.forces()
+    Fo, _, So = o.forces()
+    ok, e = PAR.compare_forces(Fg, Fo, PAR.TOL_FP32_SUSPENSION_FORCE, 11.5, atol=PAR.ps_force_floor(fo[3], So))
+    assert ok, e
+    ok, e = PAR.compare_state(Sg, So)
+    assert ok, e
+
+
 def test_ps_fp16_storage(stream):
     prob = ps(W.cylinder_drag())
     g, o = run_both(prob, 600, stream, storage="fp16")
