@@ -264,10 +264,8 @@ int upload_particles(dilbm_ctx *c, const dilbm_particle *p, int np) {
     DILBM_CUDA(cudaMemcpyAsync(c->P.r, h.data() + 2 * np, sizeof(double) * 6 * np, cudaMemcpyHostToDevice, c->stream));
     DILBM_CUDA(cudaMemcpyAsync(c->P.fixed, fx.data(), sizeof(int) * np, cudaMemcpyHostToDevice, c->stream));
     DILBM_CUDA(cudaMemsetAsync(c->bins[cur].count, 0, sizeof(int) * c->ntiles, c->stream));
-    if ((rc = launch_particles(c, 0))) return rc;
-    // the host copies above read pageable memory that goes out of scope
-    DILBM_CUDA(cudaStreamSynchronize(c->stream));
-    return DILBM_OK;
+    // (no wait: a copy from pageable memory has staged the source when it returns)
+    return launch_particles(c, 0);
 }
 
 template <typename T>
@@ -442,6 +440,30 @@ int sticky_error(int bits) {
     default: return DILBM_OK;
     }
 }
+
+// Pinned host staging for dilbm_forces: one buffer per host thread, grown on
+// demand, so that its copies run asynchronously and the call waits once.
+struct PinnedStage {
+    void *p = nullptr;
+    size_t bytes = 0;
+    ~PinnedStage() {
+        if (p) cudaFreeHost(p);
+    }
+    void *get(size_t n) {
+        if (n > bytes) {
+            if (p) cudaFreeHost(p);
+            p = nullptr;
+            bytes = 0;
+            if (cudaHostAlloc(&p, n, cudaHostAllocDefault) != cudaSuccess) {
+                p = nullptr;
+                return nullptr;
+            }
+            bytes = n;
+        }
+        return p;
+    }
+};
+thread_local PinnedStage t_stage;
 
 int read_sticky(dilbm_ctx *c) {
     int h = 0;
@@ -668,27 +690,35 @@ int dilbm_sync(dilbm_ctx *c) {
 int dilbm_forces(dilbm_ctx *c, double *force, double *fcol, dilbm_particle *state) {
     if (!c) return fail(DILBM_ERR_INVALID_ARG, "NULL context");
     if (c->np > 0 && !force) return fail(DILBM_ERR_INVALID_ARG, "force must not be NULL");
-    const int np = c->np;
+    const size_t np = (size_t)c->np;
     if (np == 0) return read_sticky(c);
-    std::vector<double> h(8 * (size_t)np);
-    std::vector<int> fx(np);
-    DILBM_CUDA(cudaMemcpyAsync(force, c->force, sizeof(double) * 3 * np, cudaMemcpyDeviceToHost, c->stream));
-    if (fcol) DILBM_CUDA(cudaMemcpyAsync(fcol, c->fcol, sizeof(double) * 2 * np, cudaMemcpyDeviceToHost, c->stream));
+    // staged: force (3 np), fcol (2 np), x, y, r, ux, uy, omega, theta, rho_s
+    // (8 np) as doubles, then fixed (np) and the error word as ints
+    double *h = static_cast<double *>(t_stage.get(sizeof(double) * 13 * np + sizeof(int) * (np + 1)));
+    if (!h) return fail(DILBM_ERR_OOM, "pinned staging for dilbm_forces");
+    double *hf = h, *hc = h + 3 * np, *hs = h + 5 * np;
+    int *fx = reinterpret_cast<int *>(h + 13 * np), *herr = fx + np;
+    DILBM_CUDA(cudaMemcpyAsync(hf, c->force, sizeof(double) * 3 * np, cudaMemcpyDeviceToHost, c->stream));
+    if (fcol) DILBM_CUDA(cudaMemcpyAsync(hc, c->fcol, sizeof(double) * 2 * np, cudaMemcpyDeviceToHost, c->stream));
     if (state) {
-        DILBM_CUDA(cudaMemcpyAsync(h.data(), c->P.x[c->cur], sizeof(double) * np, cudaMemcpyDeviceToHost, c->stream));
-        DILBM_CUDA(cudaMemcpyAsync(h.data() + np, c->P.y[c->cur], sizeof(double) * np, cudaMemcpyDeviceToHost, c->stream));
-        DILBM_CUDA(cudaMemcpyAsync(h.data() + 2 * np, c->P.r, sizeof(double) * 6 * np, cudaMemcpyDeviceToHost, c->stream));
-        DILBM_CUDA(cudaMemcpyAsync(fx.data(), c->P.fixed, sizeof(int) * np, cudaMemcpyDeviceToHost, c->stream));
+        DILBM_CUDA(cudaMemcpyAsync(hs, c->P.x[c->cur], sizeof(double) * np, cudaMemcpyDeviceToHost, c->stream));
+        DILBM_CUDA(cudaMemcpyAsync(hs + np, c->P.y[c->cur], sizeof(double) * np, cudaMemcpyDeviceToHost, c->stream));
+        DILBM_CUDA(cudaMemcpyAsync(hs + 2 * np, c->P.r, sizeof(double) * 6 * np, cudaMemcpyDeviceToHost, c->stream));
+        DILBM_CUDA(cudaMemcpyAsync(fx, c->P.fixed, sizeof(int) * np, cudaMemcpyDeviceToHost, c->stream));
     }
-    int rc = read_sticky(c);   // synchronises the stream
+    DILBM_CUDA(cudaMemcpyAsync(herr, c->err, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
+    DILBM_CUDA(cudaStreamSynchronize(c->stream));
+    c->sticky |= *herr;
+    std::memcpy(force, hf, sizeof(double) * 3 * np);
+    if (fcol) std::memcpy(fcol, hc, sizeof(double) * 2 * np);
     if (state) {
-        for (int k = 0; k < np; ++k) {
+        for (size_t k = 0; k < np; ++k) {
             dilbm_particle &q = state[k];
-            q.x = h[k]; q.y = h[np + k]; q.r = h[2 * np + k]; q.ux = h[3 * np + k]; q.uy = h[4 * np + k];
-            q.omega = h[5 * np + k]; q.theta = h[6 * np + k]; q.rho_s = h[7 * np + k]; q.fixed = fx[k];
+            q.x = hs[k]; q.y = hs[np + k]; q.r = hs[2 * np + k]; q.ux = hs[3 * np + k]; q.uy = hs[4 * np + k];
+            q.omega = hs[5 * np + k]; q.theta = hs[6 * np + k]; q.rho_s = hs[7 * np + k]; q.fixed = fx[k];
         }
     }
-    return rc;
+    return sticky_error(c->sticky);
 }
 
 int dilbm_force_mean(dilbm_ctx *c, double *mean, long long *nsteps) {
