@@ -1,4 +1,4 @@
-"""Paper-geometry validation runs on the GPU (Sec. 3.1, 3.3, 3.4).
+"""Paper-geometry validation runs on the GPU (Sec. 3.1-3.4).
 
 These are physics checks of the whole path at the paper's set-ups, not
 parity tests.  The paper gives neither the lattice resolution of Sec. 3.1
@@ -11,6 +11,8 @@ Table 1's drag at 0.6 to 1.2).
 - Sec. 3.1, Table 1: C_D and the recirculation length 2L/D behind a fixed
   cylinder in a 35D x 20D channel at Re = 20 and 40 (U = 0.1, inlet
   velocity, outlet density, free-stream sides).
+- Sec. 3.2: a disc settling on the centre line of a 1.2 cm x 6 cm channel
+  against the terminal velocity of Eq. 27.
 - Sec. 3.3: a disc released at (0.19 W, 0.75 H) in a 104 x 800 channel
   (tau = 0.6, W = 4D) migrates to the centre line while it settles, in a
   decaying swing about it, and stops rotating.
@@ -82,6 +84,39 @@ def test_cylinder_table1(stream, re):
     assert abs(cd - cd_ref) < 0.03 * cd_ref, cd
     assert abs(lw - lw_ref) < 0.03 * lw_ref, lw
     assert abs(cl) < 1e-5                                # steady, symmetric wake
+
+
+def test_centre_line_settling_against_eq27(stream):
+    # Sec. 3.2: D = 0.24 cm in a 1.2 cm x 6 cm channel, nu = 0.1 cm^2/s,
+    # dx = 0.01 cm, tau = 0.8 (121 x 601 nodes, D = 24), released from rest at
+    # (0.6 cm, 3 cm).  The terminal velocity is close to Eq. 27 (with K of
+    # Eq. 26) at low density and falls below it as the density, and with it
+    # the Reynolds number, grows (measured: 0.983, 0.971, 0.916 of Eq. 27).
+    dx, tau = 0.01, 0.8
+    nu = (tau - 0.5) / 3.0
+    dt = nu * dx * dx / 0.1
+    g = 981.0 * dt * dt / dx
+    dd = 0.24 / dx
+    ws = 120 / dd
+    K = 1.0 / (math.log(ws) - 0.9175 + 1.7244 / ws ** 2 - 1.7302 / ws ** 4 + 2.4056 / ws ** 6 - 4.5913 / ws ** 8)
+    ratio = {}
+    for rho_s in (1.01, 1.02, 1.05):
+        u27 = dd ** 2 * (rho_s - 1.0) * g / (16 * K * nu)      # Eq. 27, lattice units (rho_f = 1)
+        prob = W.sedimentation(nx=121, ny=601, r=dd / 2, rho_s=rho_s, g=g, tau=tau, eps=1.0, x0=60.0, y0=300.0,
+                               force_model=W.FORCE_MOMENTUM)
+        sim = D.Simulation(prob, stream=stream)
+        sim.step(18000)
+        v1 = -sim.forces()[2][0, 4]
+        sim.step(2000)
+        st = sim.forces()[2][0]
+        sim.close()
+        assert abs(-st[4] - v1) < 0.01 * v1                 # terminal
+        assert abs(st[0] - 60.0) < 1e-6                      # on the centre line
+        ratio[rho_s] = -st[4] / u27
+    assert 0.95 < ratio[1.01] < 1.02, ratio
+    assert 0.94 < ratio[1.02] < 1.02, ratio
+    assert 0.85 < ratio[1.05] < 0.95, ratio
+    assert ratio[1.01] > ratio[1.02] > ratio[1.05]
 
 
 def off_centre(rho_s, steps, stream):
