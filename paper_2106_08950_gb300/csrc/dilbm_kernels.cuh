@@ -1365,13 +1365,20 @@ __device__ __forceinline__ void particle_body(const PartArgs &A, int p, int lane
                 cy += sc * dy;
             }
         }
+        // (FP64 is a narrow pipe here: the repulsion sums, zero unless some
+        // lane found a contact, are reduced only when one did)
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) {
             fx += __shfl_xor_sync(0xffffffffu, fx, o);
             fy += __shfl_xor_sync(0xffffffffu, fy, o);
             tq += __shfl_xor_sync(0xffffffffu, tq, o);
-            cx += __shfl_xor_sync(0xffffffffu, cx, o);
-            cy += __shfl_xor_sync(0xffffffffu, cy, o);
+        }
+        if (__any_sync(0xffffffffu, cx != 0.0 || cy != 0.0)) {
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) {
+                cx += __shfl_xor_sync(0xffffffffu, cx, o);
+                cy += __shfl_xor_sync(0xffffffffu, cy, o);
+            }
         }
         // wall repulsion: mirror image across each non-periodic wall
         for (int w = 0; w < 4; ++w) {
@@ -1389,14 +1396,18 @@ __device__ __forceinline__ void particle_body(const PartArgs &A, int p, int lane
             cx += sc * dx;
             cy += sc * dy;
         }
-        // ---- 3. rigid-body update (every lane computes the same values)
+        // ---- 3. rigid-body update (every lane computes the same values; a
+        // masked lane saves nothing on the FP64 pipe)
         if (!P.fixed[p]) {
-            const double m = P.rho_s[p] * 3.14159265358979323846 * r * r;
-            const double I = 0.5 * m * r * r;
-            const double wgt = (1.0 - bp.rho_f / P.rho_s[p]) * m;   // buoyancy-reduced weight / g
-            ux += (fx + cx + wgt * bp.gx) / m;
-            uy += (fy + cy + wgt * bp.gy) / m;
-            om += tq / I;
+            // two FP64 divisions instead of four: the buoyancy-reduced weight
+            // (1 - rho_f / rho_s) m g is (rho_s - rho_f) pi r^2 g
+            const double area = 3.14159265358979323846 * r * r;
+            const double m = P.rho_s[p] * area;
+            const double im = 1.0 / m, iI = 1.0 / (0.5 * m * r * r);
+            const double wgt = (P.rho_s[p] - bp.rho_f) * area;      // buoyancy-reduced weight / g
+            ux += (fx + cx + wgt * bp.gx) * im;
+            uy += (fy + cy + wgt * bp.gy) * im;
+            om += tq * iI;
             nX = X + ux;
             nY = Y + uy;
             if (L.per_x) { nX = fmod(nX, (double)L.nx); if (nX < 0.0) nX += L.nx; }
