@@ -188,6 +188,19 @@ int dilbm_force_mean_reset(dilbm_ctx *ctx);
 int dilbm_set_moving_frame(dilbm_ctx *ctx, int particle, double x_ref);
 
 /*
+ * Failure-detection check, with no fault: one warp waits, with the bounded
+ * wait the sweep uses on its staging barriers (1 s limit, timed by the
+ * device's global timer), on a shared-memory barrier that nothing ever
+ * arrives at.  The wait gives up, the kernel records the timeout in a private
+ * error word as the sweep does and returns; the call reads it back.  Returns
+ * DILBM_ERR_TIMEOUT (the expected outcome) with *waited_seconds (nullable)
+ * the wait measured on the device, DILBM_OK if the wait completed, or
+ * DILBM_ERR_CUDA.  Synchronises the stream; allocates 16 bytes for the call.
+ * The device stays usable.
+ */
+int dilbm_wait_probe(void *cuda_stream, double *waited_seconds);
+
+/*
  * Columns the frame has moved since create (0 if it never moved).  offset:
  * host.  Synchronises the stream.  Errors: INVALID_ARG, CUDA.
  */

@@ -520,6 +520,25 @@ int check_problem(const dilbm_grid *g, dilbm_lattice lattice, double tau, double
 }
 }  // namespace dilbm
 
+// Failure detection without a fault: one warp waits, with the sweep's bounded
+// mbarrier wait, on a shared-memory barrier that no copy and no thread ever
+// arrives at.  The wait gives up after its limit and the kernel records
+// ERR_TIMEOUT in the caller's error word, as the sweep does, then returns.
+__global__ void wait_probe_kernel(int *err, unsigned long long *waited_ns) {
+    __shared__ __align__(8) uint64_t bar;
+    if (threadIdx.x == 0) {
+        mbar_init(&bar, 1);
+        mbar_fence_init();
+    }
+    __syncwarp();
+    const unsigned long long t0 = global_ns();
+    const bool arrived = __all_sync(0xffffffffu, mbar_wait_bounded(&bar, 0));
+    if (threadIdx.x == 0) {
+        *waited_ns = global_ns() - t0;
+        if (!arrived) atomicOr(err, ERR_TIMEOUT);
+    }
+}
+
 extern "C" {
 
 const char *dilbm_last_error(void) { return g_err.c_str(); }
@@ -758,6 +777,29 @@ int dilbm_frame_offset(dilbm_ctx *c, long long *offset) {
     if (!c->frame_off) return DILBM_OK;
     DILBM_CUDA(cudaMemcpyAsync(offset, c->frame_off, sizeof(long long), cudaMemcpyDeviceToHost, c->stream));
     DILBM_CUDA(cudaStreamSynchronize(c->stream));
+    return DILBM_OK;
+}
+
+int dilbm_wait_probe(void *cuda_stream, double *waited_seconds) {
+    cudaStream_t st = (cudaStream_t)cuda_stream;
+    void *q = nullptr;
+    DILBM_CUDA(cudaMalloc(&q, 16));
+    int *err = static_cast<int *>(q);
+    unsigned long long *waited = reinterpret_cast<unsigned long long *>(static_cast<char *>(q) + 8);
+    cudaError_t e = cudaMemsetAsync(q, 0, 16, st);
+    if (e == cudaSuccess) {
+        wait_probe_kernel<<<1, 32, 0, st>>>(err, waited);
+        e = cudaGetLastError();
+    }
+    int h_err = 0;
+    unsigned long long h_ns = 0;
+    if (e == cudaSuccess) e = cudaMemcpyAsync(&h_err, err, sizeof(int), cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(&h_ns, waited, sizeof(h_ns), cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    cudaFree(q);
+    if (e != cudaSuccess) return cuda_fail(e, "dilbm_wait_probe");
+    if (waited_seconds) *waited_seconds = (double)h_ns * 1e-9;
+    if (h_err & ERR_TIMEOUT) return fail(DILBM_ERR_TIMEOUT, "bounded device wait gave up (as intended by the probe)");
     return DILBM_OK;
 }
 

@@ -140,6 +140,7 @@ def load_library(path: Optional[str] = None):
     L.dilbm_force_mean.argtypes = [vp, vp, C.POINTER(C.c_longlong)]
     L.dilbm_force_mean_reset.argtypes = [vp]
     L.dilbm_set_moving_frame.argtypes = [vp, C.c_int, C.c_double]
+    L.dilbm_wait_probe.argtypes = [vp, C.POINTER(C.c_double)]
     L.dilbm_frame_offset.argtypes = [vp, C.POINTER(C.c_longlong)]
     L.dilbm_server_clock.argtypes = [vp]
     L.dilbm_server_clock.restype = C.c_double
@@ -152,11 +153,16 @@ def load_library(path: Optional[str] = None):
                  "dilbm_server_create", "dilbm_server_submit", "dilbm_server_progress", "dilbm_server_status",
                  "dilbm_server_result", "dilbm_force_mean", "dilbm_force_mean_reset", "dilbm_autotune",
                  "dilbm_set_shape", "dilbm_batch_autotune", "dilbm_batch_set_shape", "dilbm_set_moving_frame",
-                 "dilbm_frame_offset"):
+                 "dilbm_frame_offset", "dilbm_wait_probe"):
         getattr(L, name).restype = C.c_int
     if path == LIB_PATH:
         _lib = L
     return L
+
+
+def last_error() -> str:
+    """The library's message for the last failed call on this thread."""
+    return load_library().dilbm_last_error().decode(errors="replace")
 
 
 def check(rc: int) -> None:
@@ -206,6 +212,15 @@ def footprint(prob: W.Problem, storage: str = "fp32") -> int:
     out = C.c_ulonglong()
     check(load_library().dilbm_footprint(C.byref(g), len(prob.particles), C.byref(out)))
     return int(out.value)
+
+
+def wait_probe(stream: int):
+    """Failure-detection check (no fault): a bounded device wait on a barrier
+    nothing arrives at.  Returns (return code, seconds waited on the device);
+    the expected code is ERR_TIMEOUT."""
+    t = C.c_double()
+    rc = load_library().dilbm_wait_probe(C.c_void_p(stream), C.byref(t))
+    return int(rc), float(t.value)
 
 
 def current_stream_handle() -> int:
