@@ -1,6 +1,7 @@
 // C ABI of the DI-LBM library (declared in include/dilbm.h): context
 // management, argument checks, and the launch sequence of one time step.
 #include "dilbm.h"
+#include "dilbm_trace.h"
 #include "dilbm_launch.cuh"
 
 #include <algorithm>
@@ -545,6 +546,7 @@ const char *dilbm_last_error(void) { return g_err.c_str(); }
 
 int dilbm_create(const dilbm_grid *g, dilbm_lattice lattice, double tau, double interface_width,
                  const dilbm_particle *particles, int np, void *cuda_stream, dilbm_ctx **out) {
+    const dilbm::TraceRange trace("dilbm_create");
     if (!g || !out) return fail(DILBM_ERR_INVALID_ARG, "grid and out must not be NULL");
     *out = nullptr;
     int rc = dilbm::check_problem(g, lattice, tau, interface_width, particles, np);
@@ -677,6 +679,7 @@ int dilbm_create(const dilbm_grid *g, dilbm_lattice lattice, double tau, double 
 }
 
 int dilbm_step(dilbm_ctx *c, long long nsteps) {
+    const dilbm::TraceRange trace("dilbm_step");
     if (!c || nsteps < 0) return fail(DILBM_ERR_INVALID_ARG, "bad context or step count");
     // whole step pairs replay a captured graph (timing brackets every sweep
     // launch with events instead; a stream the caller is capturing gets the
@@ -1170,6 +1173,7 @@ int dilbm_batch_create(dilbm_ctx *const *members, int n, void *cuda_stream, dilb
 }
 
 int dilbm_batch_step(dilbm_batch *b, long long nsteps) {
+    const dilbm::TraceRange trace("dilbm_batch_step");
     if (!b || nsteps < 0) return fail(DILBM_ERR_INVALID_ARG, "bad batch or step count");
     if (nsteps == 0) return DILBM_OK;
     cudaError_t e;
@@ -1388,6 +1392,7 @@ int dilbm_set_shape(dilbm_ctx *c, int warps, int blocks_per_sm) {
 }
 
 int dilbm_autotune(dilbm_ctx *c, int reps, int *warps, int *blocks_per_sm) {
+    const dilbm::TraceRange trace("dilbm_autotune");
     if (!c) return fail(DILBM_ERR_INVALID_ARG, "NULL context");
     if (reps <= 0) reps = 10;
     if (c->method == DILBM_METHOD_PS) {         // one shape only: nothing to time
@@ -1422,6 +1427,7 @@ int dilbm_batch_set_shape(dilbm_batch *b, int warps, int blocks_per_sm) {
 }
 
 int dilbm_batch_autotune(dilbm_batch *b, int reps, int *warps, int *blocks_per_sm) {
+    const dilbm::TraceRange trace("dilbm_batch_autotune");
     if (!b) return fail(DILBM_ERR_INVALID_ARG, "NULL batch");
     if (reps <= 0) reps = 10;
     long long items = 0;

@@ -10,6 +10,7 @@
 // itself (Eqs. 13-19, 22-24, 28-29) is untouched, so every job's result is
 // the one dilbm_step gives it alone.
 #include "dilbm.h"
+#include "dilbm_trace.h"
 
 #include <cuda_runtime.h>
 
@@ -229,6 +230,7 @@ int dilbm_server_submit(dilbm_server *s, const dilbm_job *job, long long *id) {
 }
 
 int dilbm_server_progress(dilbm_server *s, dilbm_server_stats *stats) {
+    const dilbm::TraceRange trace("dilbm_server_progress");
     if (!s) return sfail(DILBM_ERR_INVALID_ARG, "NULL server");
     const double t_in = s->now();
     int rc = DILBM_OK;
