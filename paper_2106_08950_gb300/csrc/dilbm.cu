@@ -175,7 +175,7 @@ PartArgs particle_args(const dilbm_ctx *c, int cur, int integrate) {
 
 int launch_particles(dilbm_ctx *c, int integrate) {
     const int np = c->np;
-    particles_kernel<false><<<(np * 32 + 127) / 128, 128, 0, c->stream>>>(particle_args(c, c->cur, integrate),
+    particles_kernel<false><<<(np + PART_WARPS - 1) / PART_WARPS, PART_WARPS * 32, 0, c->stream>>>(particle_args(c, c->cur, integrate),
                                                                           nullptr, BatchIndex{});
     DILBM_CUDA(cudaGetLastError());
     c->launches += 1;
@@ -1054,7 +1054,7 @@ int batch_phase(dilbm_batch *b, int phase) {
     b->launches += (long long)b->sweep_params[phase].size();
     if (b->nparts > 0) {
         BatchIndex pi{b->part_start, nullptr, (int)b->members.size()};
-        particles_kernel<true><<<(b->nparts * 32 + 127) / 128, 128, 0, b->stream>>>(PartArgs{}, b->part_args[phase], pi);
+        particles_kernel<true><<<(b->nparts + PART_WARPS - 1) / PART_WARPS, PART_WARPS * 32, 0, b->stream>>>(PartArgs{}, b->part_args[phase], pi);
         DILBM_CUDA(cudaGetLastError());
         b->launches += 1;
     }

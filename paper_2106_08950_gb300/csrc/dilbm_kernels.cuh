@@ -1235,7 +1235,7 @@ __device__ __forceinline__ int range_len(const AxisTiles &a) {
     return n;
 }
 
-// One particle, by one warp.  With integrate != 0:
+// The particle update, per particle.  With integrate != 0:
 //   1. hydrodynamic force and torque (Eqs. 18-19): the row-segment partials of
 //      the tiles the particle was binned into, summed in FP64 in a fixed
 //      order (lanes take fixed (tile, row) entries, then a fixed shuffle tree);
@@ -1244,9 +1244,7 @@ __device__ __forceinline__ int range_len(const AxisTiles &a) {
 //   3. symplectic Euler of Eqs. 22-24 (dt = 1), positions read from copy
 //      `pin` and written to copy `pout`.
 // Always, finally: binning of the particle into every tile its phi tail
-// reaches (lanes take the tiles in a fixed order), with the record the sweep
-// reads: the centre relative to the tile origin (minimum image about the tile
-// centre) as FP32 hi + lo, radius and velocities.
+// reaches (see particles_kernel for how the work is split).
 // Everything one lattice's particle update needs.
 struct PartArgs {
     Lattice L;
@@ -1277,109 +1275,154 @@ __host__ __device__ inline int frame_move(double xt, double xref, int nx, int pe
     return d >= 1.0 ? 1 : (d <= -1.0 ? -1 : 0);
 }
 
-__device__ __forceinline__ void particle_body(const PartArgs &A, int p, int lane) {
+// The particles kernel takes PART_WARPS particles per block, in three phases:
+// (A) each particle's warp sums its force partials and finds its Wan-Turek
+// contacts; (B) one lane per particle does the scalar FP64 work (walls,
+// rigid-body update, frame move, velocity splits, tile ranges); (C) each warp
+// bins its particle for the next sweep.  The FP64 pipe is narrow on this part
+// and charges per warp instruction whatever the mask, so one warp serving the
+// block's particles in (B) costs a PART_WARPS-th of every warp doing its own.
+constexpr int PART_WARPS = 8;
+
+struct PartShared {
+    double fx, fy, tq, cx, cy;      // (A) hydrodynamic force, torque; repulsion
+    double nX, nY;                  // (B) position for the next step
+    float4 rb;                      // (B) record: r and the velocities' FP32 hi parts
+    float rlx, rly, rlz;            // (B) the velocities' FP32 lo parts
+    AxisTiles ax, ay;               // (B) the tiles the particle's reach covers
+};
+
+// The position copies of a step without indexing the parameter arrays.
+struct PartCopies {
+    const double *xin, *yin;
+    const float *xfin, *yfin;
+    double *xout, *yout;
+    float *xfout, *yfout;
+    __device__ __forceinline__ explicit PartCopies(const PartArgs &A) {
+        const Particles &P = A.P;
+        xin = A.pin ? P.x[1] : P.x[0]; yin = A.pin ? P.y[1] : P.y[0];
+        xfin = A.pin ? P.xf[1] : P.xf[0]; yfin = A.pin ? P.yf[1] : P.yf[0];
+        xout = A.pout ? P.x[1] : P.x[0]; yout = A.pout ? P.y[1] : P.y[0];
+        xfout = A.pout ? P.xf[1] : P.xf[0]; yfout = A.pout ? P.yf[1] : P.yf[0];
+    }
+};
+
+// (A) Hydrodynamic force and torque (Eqs. 18-19) from the sweep's partials,
+// and the particle-particle repulsion (Eq. 28), summed over the warp.
+__device__ __forceinline__ void particle_forces(const PartArgs &A, int p, int lane, PartShared &sh) {
+    const Lattice &L = A.L;
+    const Particles &P = A.P;
+    const BodyParams &bp = A.bp;
+    const Bins &bin_in = A.bin_in;
+    const float4 *__restrict__ partial = A.partial;
+    const PartCopies pc(A);
+    const double *xin = pc.xin, *yin = pc.yin;
+    const float *xfin = pc.xfin, *yfin = pc.yfin;
+    const double X = xin[p], Y = yin[p], r = P.r[p];
+
+    // ---- 1. hydrodynamic force and torque
+    double fx = 0.0, fy = 0.0, tq = 0.0;
+    const int nk = bin_in.npslot[p];
+    for (int e = lane; e < nk * TILE_H; e += 32) {
+        const int k = e / TILE_H, row = e - k * TILE_H;
+        const int ts = bin_in.pslot[(long long)p * MAXT + k];
+        if (ts < 0) continue;
+        const int ty = (ts / MAXC) / L.ntx;
+        if (ty * TILE_H + row >= L.ny) continue;
+        const float4 v = partial[(long long)ts * TILE_H + row];
+        fx += (double)v.x; fy += (double)v.y; tq += (double)v.z;
+    }
+    // ---- 2. particle-particle repulsion.  A pair within r_i + r_j + xi
+    // shares the tile holding the middle of the gap between the surfaces
+    // (that point lies inside both binning reaches), so each lane takes
+    // some of this particle's tiles and counts a pair only in that tile;
+    // within a tile the pairs are added in increasing partner id.
+    double cx = 0.0, cy = 0.0;
+    const float xf = xfin[p], yf = yfin[p], rf = (float)r;
+    for (int k = lane; k < nk; k += 32) {
+        const int ts = bin_in.pslot[(long long)p * MAXT + k];
+        if (ts < 0) continue;
+        const int t = ts / MAXC;
+        int n = bin_in.count[t];
+        n = n > MAXC ? MAXC : n;
+        uint32_t contact = 0;
+        for (int sl = 0; sl < n; ++sl) {
+            const int j = bin_in.ids[t * MAXC + sl];
+            if (j == p) continue;
+            float dxf = xf - xfin[j], dyf = yf - yfin[j];
+            if (L.per_x) { if (dxf >= 0.5f * L.nx) dxf -= L.nx; else if (dxf < -0.5f * L.nx) dxf += L.nx; }
+            if (L.per_y) { if (dyf >= 0.5f * L.ny) dyf -= L.ny; else if (dyf < -0.5f * L.ny) dyf += L.ny; }
+            const float lim = rf + (float)P.r[j] + (float)bp.xi + 0.05f;
+            if (dxf * dxf + dyf * dyf > lim * lim) continue;
+            double dx = X - xin[j], dy = Y - yin[j];
+            if (L.per_x) { while (dx >= 0.5 * L.nx) dx -= L.nx; while (dx < -0.5 * L.nx) dx += L.nx; }
+            if (L.per_y) { while (dy >= 0.5 * L.ny) dy -= L.ny; while (dy < -0.5 * L.ny) dy += L.ny; }
+            // the middle of the gap between the two surfaces, at distance
+            // (d + r - r_j) / 2 from this centre toward the partner
+            const double dd = sqrt(dx * dx + dy * dy);
+            const double f = dd > 0.0 ? 0.5 * (dd + r - P.r[j]) / dd : 0.0;
+            double mx = X - f * dx, my = Y - f * dy;
+            if (L.per_x) { mx = fmod(mx, (double)L.nx); if (mx < 0.0) mx += L.nx; }
+            if (L.per_y) { my = fmod(my, (double)L.ny); if (my < 0.0) my += L.ny; }
+            int mxi = (int)floor(mx), myi = (int)floor(my);
+            mxi = mxi < 0 ? 0 : (mxi > L.nx - 1 ? L.nx - 1 : mxi);
+            myi = myi < 0 ? 0 : (myi > L.ny - 1 ? L.ny - 1 : myi);
+            if ((myi / TILE_H) * L.ntx + mxi / TILE_W == t) contact |= 1u << sl;
+        }
+        while (contact) {                         // increasing partner id
+            int sel = -1, jmin = 0x7fffffff;
+            for (uint32_t m = contact; m; m &= m - 1) {
+                const int sl = __ffs(m) - 1, j = bin_in.ids[t * MAXC + sl];
+                if (j < jmin) { jmin = j; sel = sl; }
+            }
+            contact &= ~(1u << sel);
+            double dx = X - xin[jmin], dy = Y - yin[jmin];
+            if (L.per_x) { while (dx >= 0.5 * L.nx) dx -= L.nx; while (dx < -0.5 * L.nx) dx += L.nx; }
+            if (L.per_y) { while (dy >= 0.5 * L.ny) dy -= L.ny; while (dy < -0.5 * L.ny) dy += L.ny; }
+            const double d = sqrt(dx * dx + dy * dy), rr = r + P.r[jmin];
+            double sc = 0.0;
+            if (d <= rr) sc = (rr - d) / bp.eps_p2;
+            else if (d <= rr + bp.xi) sc = (rr + bp.xi - d) * (rr + bp.xi - d) / bp.eps_p;
+            cx += sc * dx;
+            cy += sc * dy;
+        }
+    }
+    // (the repulsion sums, zero unless some lane found a contact, are
+    // reduced only when one did)
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        fx += __shfl_xor_sync(0xffffffffu, fx, o);
+        fy += __shfl_xor_sync(0xffffffffu, fy, o);
+        tq += __shfl_xor_sync(0xffffffffu, tq, o);
+    }
+    if (__any_sync(0xffffffffu, cx != 0.0 || cy != 0.0)) {
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            cx += __shfl_xor_sync(0xffffffffu, cx, o);
+            cy += __shfl_xor_sync(0xffffffffu, cy, o);
+        }
+    }
+    if (lane == 0) {
+        sh.fx = fx; sh.fy = fy; sh.tq = tq; sh.cx = cx; sh.cy = cy;
+    }
+}
+
+// (B) One thread per particle: wall repulsion (Eq. 29), the rigid-body
+// update (Eqs. 22-24), the frame move, the position copies for the next step,
+// and what the binning needs (velocity splits, the tiles the reach covers).
+__device__ __forceinline__ void particle_update(const PartArgs &A, int p, PartShared &sh) {
     const Lattice &L = A.L;
     const Physics &ph = A.ph;
     const Particles &P = A.P;
     const BodyParams &bp = A.bp;
-    const Bins &bin_in = A.bin_in, &bin_out = A.bin_out;
-    const float4 *__restrict__ partial = A.partial;
-    const int pin = A.pin, pout = A.pout, integrate = A.integrate;
-    double *__restrict__ force = A.force;
-    double *__restrict__ fcol = A.fcol;
-    int *__restrict__ err = A.err;
-    // pick the position copies without indexing the parameter arrays
-    const double *xin = pin ? P.x[1] : P.x[0], *yin = pin ? P.y[1] : P.y[0];
-    const float *xfin = pin ? P.xf[1] : P.xf[0], *yfin = pin ? P.yf[1] : P.yf[0];
-    double *xout = pout ? P.x[1] : P.x[0], *yout = pout ? P.y[1] : P.y[0];
-    float *xfout = pout ? P.xf[1] : P.xf[0], *yfout = pout ? P.yf[1] : P.yf[0];
-    const double X = xin[p], Y = yin[p], r = P.r[p];
+    const PartCopies pc(A);
+    const double X = pc.xin[p], Y = pc.yin[p], r = P.r[p];
     double nX = X, nY = Y;
     double ux = P.ux[p], uy = P.uy[p], om = P.omega[p];
 
-    if (integrate) {
-        // ---- 1. hydrodynamic force and torque
-        double fx = 0.0, fy = 0.0, tq = 0.0;
-        const int nk = bin_in.npslot[p];
-        for (int e = lane; e < nk * TILE_H; e += 32) {
-            const int k = e / TILE_H, row = e - k * TILE_H;
-            const int ts = bin_in.pslot[(long long)p * MAXT + k];
-            if (ts < 0) continue;
-            const int ty = (ts / MAXC) / L.ntx;
-            if (ty * TILE_H + row >= L.ny) continue;
-            const float4 v = partial[(long long)ts * TILE_H + row];
-            fx += (double)v.x; fy += (double)v.y; tq += (double)v.z;
-        }
-        // ---- 2. particle-particle repulsion.  A pair within r_i + r_j + xi
-        // shares the tile holding the middle of the gap between the surfaces
-        // (that point lies inside both binning reaches), so each lane takes
-        // some of this particle's tiles and counts a pair only in that tile;
-        // within a tile the pairs are added in increasing partner id.
-        double cx = 0.0, cy = 0.0;
-        const float xf = xfin[p], yf = yfin[p], rf = (float)r;
-        for (int k = lane; k < nk; k += 32) {
-            const int ts = bin_in.pslot[(long long)p * MAXT + k];
-            if (ts < 0) continue;
-            const int t = ts / MAXC;
-            int n = bin_in.count[t];
-            n = n > MAXC ? MAXC : n;
-            uint32_t contact = 0;
-            for (int sl = 0; sl < n; ++sl) {
-                const int j = bin_in.ids[t * MAXC + sl];
-                if (j == p) continue;
-                float dxf = xf - xfin[j], dyf = yf - yfin[j];
-                if (L.per_x) { if (dxf >= 0.5f * L.nx) dxf -= L.nx; else if (dxf < -0.5f * L.nx) dxf += L.nx; }
-                if (L.per_y) { if (dyf >= 0.5f * L.ny) dyf -= L.ny; else if (dyf < -0.5f * L.ny) dyf += L.ny; }
-                const float lim = rf + (float)P.r[j] + (float)bp.xi + 0.05f;
-                if (dxf * dxf + dyf * dyf > lim * lim) continue;
-                double dx = X - xin[j], dy = Y - yin[j];
-                if (L.per_x) { while (dx >= 0.5 * L.nx) dx -= L.nx; while (dx < -0.5 * L.nx) dx += L.nx; }
-                if (L.per_y) { while (dy >= 0.5 * L.ny) dy -= L.ny; while (dy < -0.5 * L.ny) dy += L.ny; }
-                // the middle of the gap between the two surfaces, at distance
-                // (d + r - r_j) / 2 from this centre toward the partner
-                const double dd = sqrt(dx * dx + dy * dy);
-                const double f = dd > 0.0 ? 0.5 * (dd + r - P.r[j]) / dd : 0.0;
-                double mx = X - f * dx, my = Y - f * dy;
-                if (L.per_x) { mx = fmod(mx, (double)L.nx); if (mx < 0.0) mx += L.nx; }
-                if (L.per_y) { my = fmod(my, (double)L.ny); if (my < 0.0) my += L.ny; }
-                int mxi = (int)floor(mx), myi = (int)floor(my);
-                mxi = mxi < 0 ? 0 : (mxi > L.nx - 1 ? L.nx - 1 : mxi);
-                myi = myi < 0 ? 0 : (myi > L.ny - 1 ? L.ny - 1 : myi);
-                if ((myi / TILE_H) * L.ntx + mxi / TILE_W == t) contact |= 1u << sl;
-            }
-            while (contact) {                         // increasing partner id
-                int sel = -1, jmin = 0x7fffffff;
-                for (uint32_t m = contact; m; m &= m - 1) {
-                    const int sl = __ffs(m) - 1, j = bin_in.ids[t * MAXC + sl];
-                    if (j < jmin) { jmin = j; sel = sl; }
-                }
-                contact &= ~(1u << sel);
-                double dx = X - xin[jmin], dy = Y - yin[jmin];
-                if (L.per_x) { while (dx >= 0.5 * L.nx) dx -= L.nx; while (dx < -0.5 * L.nx) dx += L.nx; }
-                if (L.per_y) { while (dy >= 0.5 * L.ny) dy -= L.ny; while (dy < -0.5 * L.ny) dy += L.ny; }
-                const double d = sqrt(dx * dx + dy * dy), rr = r + P.r[jmin];
-                double sc = 0.0;
-                if (d <= rr) sc = (rr - d) / bp.eps_p2;
-                else if (d <= rr + bp.xi) sc = (rr + bp.xi - d) * (rr + bp.xi - d) / bp.eps_p;
-                cx += sc * dx;
-                cy += sc * dy;
-            }
-        }
-        // (FP64 is a narrow pipe here: the repulsion sums, zero unless some
-        // lane found a contact, are reduced only when one did)
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) {
-            fx += __shfl_xor_sync(0xffffffffu, fx, o);
-            fy += __shfl_xor_sync(0xffffffffu, fy, o);
-            tq += __shfl_xor_sync(0xffffffffu, tq, o);
-        }
-        if (__any_sync(0xffffffffu, cx != 0.0 || cy != 0.0)) {
-#pragma unroll
-            for (int o = 16; o > 0; o >>= 1) {
-                cx += __shfl_xor_sync(0xffffffffu, cx, o);
-                cy += __shfl_xor_sync(0xffffffffu, cy, o);
-            }
-        }
+    if (A.integrate) {
+        const double fx = sh.fx, fy = sh.fy, tq = sh.tq;
+        double cx = sh.cx, cy = sh.cy;
         // wall repulsion: mirror image across each non-periodic wall
         for (int w = 0; w < 4; ++w) {
             if (L.side_kind[w] == SIDE_PERIODIC) continue;
@@ -1396,8 +1439,7 @@ __device__ __forceinline__ void particle_body(const PartArgs &A, int p, int lane
             cx += sc * dx;
             cy += sc * dy;
         }
-        // ---- 3. rigid-body update (every lane computes the same values; a
-        // masked lane saves nothing on the FP64 pipe)
+        // ---- 3. rigid-body update
         if (!P.fixed[p]) {
             // two FP64 divisions instead of four: the buoyancy-reduced weight
             // (1 - rho_f / rho_s) m g is (rho_s - rho_f) pi r^2 g
@@ -1412,46 +1454,52 @@ __device__ __forceinline__ void particle_body(const PartArgs &A, int p, int lane
             nY = Y + uy;
             if (L.per_x) { nX = fmod(nX, (double)L.nx); if (nX < 0.0) nX += L.nx; }
             if (L.per_y) { nY = fmod(nY, (double)L.ny); if (nY < 0.0) nY += L.ny; }
+            P.ux[p] = ux; P.uy[p] = uy; P.omega[p] = om;
+            P.theta[p] += om;
         }
-        if (lane == 0) {
-            force[3 * p] = fx; force[3 * p + 1] = fy; force[3 * p + 2] = tq;
-            fcol[2 * p] = cx; fcol[2 * p + 1] = cy;
-            if (A.fsum) {
-                A.fsum[3 * p] += fx; A.fsum[3 * p + 1] += fy; A.fsum[3 * p + 2] += tq;
+        A.force[3 * p] = fx; A.force[3 * p + 1] = fy; A.force[3 * p + 2] = tq;
+        A.fcol[2 * p] = cx; A.fcol[2 * p + 1] = cy;
+        if (A.fsum) {
+            A.fsum[3 * p] += fx; A.fsum[3 * p + 1] += fy; A.fsum[3 * p + 2] += tq;
+        }
+        if (A.track >= 0) {
+            // the frame moves with the tracked particle: every particle, fixed
+            // ones included, shifts by the same whole number of columns
+            const int s = frame_move(pc.xin[A.track], A.track_x, L.nx, L.per_x);
+            if (s) {
+                nX -= (double)s;
+                if (L.per_x) { nX = fmod(nX, (double)L.nx); if (nX < 0.0) nX += L.nx; }
             }
-            if (!P.fixed[p]) {
-                P.ux[p] = ux; P.uy[p] = uy; P.omega[p] = om;
-                P.theta[p] += om;
-            }
         }
     }
-    if (integrate && A.track >= 0) {
-        // the frame moves with the tracked particle: every particle, fixed
-        // ones included, shifts by the same whole number of columns
-        const int s = frame_move(xin[A.track], A.track_x, L.nx, L.per_x);
-        if (s) {
-            nX -= (double)s;
-            if (L.per_x) { nX = fmod(nX, (double)L.nx); if (nX < 0.0) nX += L.nx; }
-        }
-    }
-    if (lane == 0) {
-        xout[p] = nX; yout[p] = nY;
-        xfout[p] = (float)nX; yfout[p] = (float)nY;
-    }
+    pc.xout[p] = nX; pc.yout[p] = nY;
+    pc.xfout[p] = (float)nX; pc.yfout[p] = (float)nY;
 
-    // ---- binning for the next sweep
     // velocities as FP32 hi + lo: the sweep forms u_s - u*, a small difference
     const float uxh = (float)ux, uyh = (float)uy, omh = (float)om;
-    const float4 rb = make_float4((float)r, uxh, uyh, omh);
-    const float rlx = (float)(ux - (double)uxh), rly = (float)(uy - (double)uyh), rlz = (float)(om - (double)omh);
+    sh.nX = nX; sh.nY = nY;
+    sh.rb = make_float4((float)r, uxh, uyh, omh);
+    sh.rlx = (float)(ux - (double)uxh); sh.rly = (float)(uy - (double)uyh); sh.rlz = (float)(om - (double)omh);
     const double R = r + ph.cut_d;
+    sh.ax = axis_tiles(nX, R, L.nx, TILE_W, L.ntx, L.per_x);
+    sh.ay = axis_tiles(nY, R, L.ny, TILE_H, L.nty, L.per_y);
+}
 
-    const AxisTiles ax = axis_tiles(nX, R, L.nx, TILE_W, L.ntx, L.per_x);
-    const AxisTiles ay = axis_tiles(nY, R, L.ny, TILE_H, L.nty, L.per_y);
+// (C) Binning of the particle into every tile its reach covers (lanes take
+// the tiles in a fixed order), with the record the sweep reads: the centre
+// relative to the tile origin (minimum image about the tile centre) as FP32
+// hi + lo, radius and velocities.
+__device__ __forceinline__ void particle_bin(const PartArgs &A, int p, int lane, const PartShared &sh) {
+    const Lattice &L = A.L;
+    const Bins &bin_out = A.bin_out;
+    const double nX = sh.nX, nY = sh.nY;
+    const AxisTiles ax = sh.ax, ay = sh.ay;
+    const float4 rb = sh.rb;
+    const float rlx = sh.rlx, rly = sh.rly, rlz = sh.rlz;
     const int NX = range_len(ax), NY = range_len(ay);
     int total = NX * NY;
     if (total > MAXT) {                      // ruled out at create; kept as a guard
-        if (lane == 0) atomicOr(err, ERR_OVERFLOW);
+        if (lane == 0) atomicOr(A.err, ERR_OVERFLOW);
         total = MAXT;
     }
     for (int k = lane; k < total; k += 32) {
@@ -1481,27 +1529,46 @@ __device__ __forceinline__ void particle_body(const PartArgs &A, int p, int lane
             bin_out.rec[NREC * (long long)entry + 2] =
                 make_float4(rlx, rly, rlz, __int_as_float((fxi & 0xffff) | (int)((unsigned)fyi << 16)));
         } else {
-            atomicOr(err, ERR_OVERFLOW);
+            atomicOr(A.err, ERR_OVERFLOW);
         }
         bin_out.pslot[(long long)p * MAXT + k] = entry;
     }
     if (lane == 0) bin_out.npslot[p] = total;
 }
 
-// One warp per particle of one lattice (BATCH = false) or of every lattice of
-// a batch (BATCH = true; bi.item_start holds each lattice's first particle).
+// PART_WARPS particles per block of one lattice (BATCH = false) or of every
+// lattice of a batch (BATCH = true; bi.item_start holds each lattice's first
+// particle).  Launch with PART_WARPS * 32 threads and ceil(particles /
+// PART_WARPS) blocks.
 template <bool BATCH>
-__global__ void particles_kernel(const __grid_constant__ PartArgs one, const PartArgs *__restrict__ many, BatchIndex bi) {
-    const int lane = threadIdx.x & 31;
-    const int gwp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-    if constexpr (BATCH) {
-        if (gwp >= bi.item_start[bi.n]) return;
-        const int lat = batch_find(bi.item_start, bi.n, gwp);
-        particle_body(many[lat], gwp - bi.item_start[lat], lane);
-    } else {
-        if (gwp >= one.bp.np) return;
-        particle_body(one, gwp, lane);
+__global__ void __launch_bounds__(PART_WARPS * 32)
+particles_kernel(const __grid_constant__ PartArgs one, const PartArgs *__restrict__ many, BatchIndex bi) {
+    __shared__ PartShared sh[PART_WARPS];
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    const int total = BATCH ? bi.item_start[bi.n] : one.bp.np;
+    // the arguments and index of item g (a particle), or null past the end
+    auto locate = [&](int g, int &p) -> const PartArgs * {
+        if (g >= total) return nullptr;
+        if constexpr (BATCH) {
+            const int lat = batch_find(bi.item_start, bi.n, g);
+            p = g - bi.item_start[lat];
+            return &many[lat];
+        } else {
+            p = g;
+            return &one;
+        }
+    };
+    int p = 0;
+    const PartArgs *A = locate(blockIdx.x * PART_WARPS + w, p);
+    if (A && A->integrate) particle_forces(*A, p, lane, sh[w]);
+    __syncthreads();
+    if (w == 0 && lane < PART_WARPS) {
+        int q = 0;
+        const PartArgs *B = locate(blockIdx.x * PART_WARPS + lane, q);
+        if (B) particle_update(*B, q, sh[lane]);
     }
+    __syncthreads();
+    if (A) particle_bin(*A, p, lane, sh[w]);
 }
 
 // ------------------------------------------------------------ conversions

@@ -225,7 +225,7 @@ extern "C" int dilbm_step_static(const dilbm_grid *g, double tau, double interfa
         particles_in_kernel<<<(np + 127) / 128, 128, 0, st>>>(particles, P, np, L.nx, L.ny, L.per_x, L.per_y, err);
         S_CUDA(cudaGetLastError());
         // bin the particles where they are (positions copy 0, bins 0)
-        particles_kernel<false><<<(np * 32 + 127) / 128, 128, 0, st>>>(part_args(0, 0, 0, bins[0], bins[0]),
+        particles_kernel<false><<<(np + PART_WARPS - 1) / PART_WARPS, PART_WARPS * 32, 0, st>>>(part_args(0, 0, 0, bins[0], bins[0]),
                                                                        nullptr, BatchIndex{});
         S_CUDA(cudaGetLastError());
     }
@@ -261,7 +261,7 @@ extern "C" int dilbm_step_static(const dilbm_grid *g, double tau, double interfa
 
     if (np > 0) {
         // force reduction, Wan-Turek, Newton-Euler (positions copy 0 -> 1)
-        particles_kernel<false><<<(np * 32 + 127) / 128, 128, 0, st>>>(part_args(0, 1, 1, bins[0], bins[1]),
+        particles_kernel<false><<<(np + PART_WARPS - 1) / PART_WARPS, PART_WARPS * 32, 0, st>>>(part_args(0, 1, 1, bins[0], bins[1]),
                                                                        nullptr, BatchIndex{});
         S_CUDA(cudaGetLastError());
         particles_out_kernel<<<(np + 127) / 128, 128, 0, st>>>(particles, P, np);
