@@ -807,45 +807,55 @@ __device__ __forceinline__ bool sweep_segment(const SweepArgs<T> &A, int y, int 
             if (lo * lo > h2) continue;
         }
         const int id = cid[c];
-        // PS: the centre's whole-cell offsets from the tile origin, packed in the record
-        const int fpk = PS ? __float_as_int(crec[2 * MAXC + c].w) : 0;
+        if constexpr (PS) {
+            // covered cell fraction (B = eps_s, Eq. 8): 1 once every corner is
+            // inside, else the particle's table entry for the cell.  The four
+            // nodes' entries are fetched before any is used, so their latencies
+            // overlap.  The centre's whole-cell offsets come packed in the record.
+            const int fpk = __float_as_int(crec[2 * MAXC + c].w);
+            const int K = ph.ck, S = 2 * K + 1;
+            const float *tab = A.B.cover + (long long)id * S * S;
+            const int iy = (y - ty0) - (int)(short)((unsigned)fpk >> 16) - L.ny * ky + K;
+            float pcq[VEC], dxq[VEC];
 #pragma unroll
-        for (int q = 0; q < VEC; ++q) {
-            float dx = dx0 + (float)q;
-            int kx = 0;
-            if constexpr (PS) {
+            for (int q = 0; q < VEC; ++q) {
+                float dx = dx0 + (float)q;
+                int kx = 0;
                 if (L.wrap_x) {
                     const float k = rintf(dx * __frcp_rn((float)L.nx));
                     dx = fmaf(-(float)L.nx, k, dx);
                     kx = (int)k;
                 }
-            } else {
-                if (L.wrap_x) dx = fmaf(-(float)L.nx, rintf(dx * __frcp_rn((float)L.nx)), dx);
+                dxq[q] = dx;
+                const float d2 = dx * dx + dy * dy;
+                const float l = rb.x - sqrtf(d2);
+                const int ix = lane * VEC + q - (int)(short)(fpk & 0xffff) - L.nx * kx + K;
+                const bool inside = d2 <= R * R && l >= -ph.cut;
+                const bool look = inside && l < ph.cut && (unsigned)ix < (unsigned)S && (unsigned)iy < (unsigned)S;
+                pcq[q] = look ? __ldg(tab + iy * S + ix) : (inside && l >= ph.cut ? 1.0f : 0.f);
             }
-            const float d2 = dx * dx + dy * dy;
-            if (d2 > R * R) continue;
-            const float l = rb.x - sqrtf(d2);
-            if (l < -ph.cut) continue;
-            float pc;
-            if constexpr (PS) {
-                // covered cell fraction (B = eps_s, Eq. 8): 1 once every corner is
-                // inside, else the particle's table entry for this cell
-                if (l >= ph.cut) {
-                    pc = 1.0f;
-                } else {
-                    const int K = ph.ck, S = 2 * K + 1;
-                    const int ix = lane * VEC + q - (int)(short)(fpk & 0xffff) - L.nx * kx + K;
-                    const int iy = (y - ty0) - (int)(short)((unsigned)fpk >> 16) - L.ny * ky + K;
-                    pc = ((unsigned)ix < (unsigned)S && (unsigned)iy < (unsigned)S)
-                             ? __ldg(A.B.cover + (long long)id * S * S + iy * S + ix) : 0.f;
-                }
+#pragma unroll
+            for (int q = 0; q < VEC; ++q) {
+                const float pc = pcq[q];
                 if (!(pc > 0.f)) continue;
-            } else {
-                // (1 + tanh(2l/eps)) / 2 == 1 / (1 + exp(-4l/eps))
-                pc = __frcp_rn(1.0f + expf(-ph.four_over_eps * l));
+                if (pc > phi[q] || (pc == phi[q] && id < best_id[q])) {
+                    phi[q] = pc; best[q] = c; best_id[q] = id; rxn[q] = dxq[q]; ryn[q] = dy;
+                }
             }
-            if (pc > phi[q] || (pc == phi[q] && pc > 0.f && id < best_id[q])) {
-                phi[q] = pc; best[q] = c; best_id[q] = id; rxn[q] = dx; ryn[q] = dy;
+        } else {
+#pragma unroll
+            for (int q = 0; q < VEC; ++q) {
+                float dx = dx0 + (float)q;
+                if (L.wrap_x) dx = fmaf(-(float)L.nx, rintf(dx * __frcp_rn((float)L.nx)), dx);
+                const float d2 = dx * dx + dy * dy;
+                if (d2 > R * R) continue;
+                const float l = rb.x - sqrtf(d2);
+                if (l < -ph.cut) continue;
+                // (1 + tanh(2l/eps)) / 2 == 1 / (1 + exp(-4l/eps))
+                const float pc = __frcp_rn(1.0f + expf(-ph.four_over_eps * l));
+                if (pc > phi[q] || (pc == phi[q] && pc > 0.f && id < best_id[q])) {
+                    phi[q] = pc; best[q] = c; best_id[q] = id; rxn[q] = dx; ryn[q] = dy;
+                }
             }
         }
     }
