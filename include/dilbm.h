@@ -344,8 +344,13 @@ typedef enum {
     DILBM_ADMIT_FIRST_FIT = 1   /* admit every queued job that fits, in arrival order */
 } dilbm_admit_policy;
 
+/* dilbm_server_config.storage: each job keeps its own grid.storage; the
+ * server steps one batch per storage type, all by the same macro-steps. */
+#define DILBM_STORAGE_PER_JOB (-1)
+
 typedef struct {
-    int storage;                /* dilbm_storage of every job (a job's grid.storage is ignored) */
+    int storage;                /* dilbm_storage of every job (a job's grid.storage is ignored),
+                                   or DILBM_STORAGE_PER_JOB */
     int max_jobs;               /* jobs resident at once, 1..1024 */
     long long macro_steps;      /* most steps per macro-step, >= 1 */
     double memory_budget;       /* bytes the resident jobs may take; <= 0: 90% of free device memory at create */

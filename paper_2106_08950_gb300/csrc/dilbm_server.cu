@@ -1,9 +1,11 @@
 // Serving (declared in include/dilbm.h): continuous batching of DI-LBM jobs.
 //
 // Every admitted job is an ordinary context (dilbm_create) that stays
-// resident on the device until it has run its steps; all running jobs advance
-// together as one batch (dilbm_batch_*), so that one sweep launch and one
-// particle launch per step cover every lattice in the mix.  The server only
+// resident on the device until it has run its steps; all running jobs of one
+// storage type advance together as one batch (dilbm_batch_*), so that one
+// sweep launch and one particle launch per step cover every lattice in the
+// mix.  With per-job storage the batches of the storage types present run
+// side by side (each on its own stream), by the same macro-steps.  The server only
 // decides who runs: it admits queued jobs by free job slots and by a device
 // memory budget, cuts the run into macro-steps no longer than the shortest
 // remaining job, and re-forms the batch when jobs join or leave.  The method
@@ -38,6 +40,7 @@ int scuda(cudaError_t e, const char *what) {
 }
 
 constexpr int MAX_JOBS = 1024;
+constexpr int NSTORE = 3;             // FP32, FP16, BF16 deviations: one batch each
 
 struct Job {
     long long id = 0;
@@ -66,8 +69,8 @@ struct dilbm_server {
     std::unordered_map<long long, std::unique_ptr<Job>> jobs;
     std::deque<Job *> queue;              // arrival (submit) order
     std::vector<Job *> running;           // admitted, not yet finished
-    std::vector<Job *> members;           // the jobs of the current batch, in member order
-    dilbm_batch *batch = nullptr;
+    std::vector<Job *> members[NSTORE];   // the jobs of each storage type's batch, in member order
+    dilbm_batch *batch[NSTORE] = {};
     bool dirty = false;                   // running set changed since the batch was formed
     long long next_id = 0;
     long long n_done = 0, n_failed = 0, macro = 0;
@@ -96,11 +99,18 @@ void release(dilbm_server *s, Job *j) {
 }
 
 void drop_batch(dilbm_server *s) {
-    if (s->batch) {
-        s->launches_gone += dilbm_batch_launch_count(s->batch);
-        dilbm_batch_destroy(s->batch);
-        s->batch = nullptr;
-    }
+    for (int c = 0; c < NSTORE; ++c)
+        if (s->batch[c]) {
+            s->launches_gone += dilbm_batch_launch_count(s->batch[c]);
+            dilbm_batch_destroy(s->batch[c]);
+            s->batch[c] = nullptr;
+        }
+}
+
+bool has_batch(const dilbm_server *s) {
+    for (int c = 0; c < NSTORE; ++c)
+        if (s->batch[c]) return true;
+    return false;
 }
 
 // Admit queued jobs while a slot is free and the budget allows.  A job that
@@ -118,7 +128,6 @@ int admit(dilbm_server *s) {
         }
         cudaError_t e = cudaStreamCreateWithFlags(&j->stream, cudaStreamNonBlocking);
         if (e != cudaSuccess) return scuda(e, "cudaStreamCreateWithFlags");
-        j->grid.storage = s->cfg.storage;
         const int rc = dilbm_create(&j->grid, DILBM_D2Q9, j->tau, j->eps, j->parts.empty() ? nullptr : j->parts.data(),
                                     (int)j->parts.size(), j->stream, &j->ctx);
         if (rc == DILBM_ERR_OOM && (!s->running.empty() || s->in_use > 0)) {
@@ -160,7 +169,8 @@ void fill_stats(const dilbm_server *s, dilbm_server_stats *st) {
     st->wait_seconds = s->t_wait;
     st->retire_seconds = s->t_retire;
     st->memory_in_use = s->in_use;
-    long long l = s->launches_gone + (s->batch ? dilbm_batch_launch_count(s->batch) : 0);
+    long long l = s->launches_gone;
+    for (int c = 0; c < NSTORE; ++c) l += s->batch[c] ? dilbm_batch_launch_count(s->batch[c]) : 0;
     for (const Job *j : s->running) l += j->ctx ? dilbm_launch_count(j->ctx) : 0;
     st->launches = l;
 }
@@ -173,7 +183,7 @@ int dilbm_server_create(const dilbm_server_config *cfg, void *cuda_stream, dilbm
     (void)cuda_stream;       // every job runs on a stream of its own
     if (!cfg || !out) return sfail(DILBM_ERR_INVALID_ARG, "config and out must not be NULL");
     *out = nullptr;
-    if (cfg->storage < DILBM_FP32 || cfg->storage > DILBM_BF16_DEV)
+    if (cfg->storage != DILBM_STORAGE_PER_JOB && (cfg->storage < DILBM_FP32 || cfg->storage > DILBM_BF16_DEV))
         return sfail(DILBM_ERR_INVALID_ARG, "unknown storage");
     if (cfg->max_jobs < 1 || cfg->max_jobs > MAX_JOBS)
         return sfail(DILBM_ERR_INVALID_ARG, "max_jobs must be 1.." + std::to_string(MAX_JOBS));
@@ -203,7 +213,7 @@ int dilbm_server_submit(dilbm_server *s, const dilbm_job *job, long long *id) {
     if (job->mean_window < 0 || job->mean_window > job->nsteps)
         return sfail(DILBM_ERR_INVALID_ARG, "mean_window must be 0..nsteps");
     dilbm_grid g = job->grid;
-    g.storage = s->cfg.storage;
+    if (s->cfg.storage != DILBM_STORAGE_PER_JOB) g.storage = s->cfg.storage;
     int rc = dilbm::check_problem(&g, DILBM_D2Q9, job->tau, job->interface_width, job->particles, job->np);
     if (rc) return rc;
     if (g.method != DILBM_METHOD_DI) return sfail(DILBM_ERR_INVALID_ARG, "the server runs DI-LBM jobs only");
@@ -240,36 +250,49 @@ int dilbm_server_progress(dilbm_server *s, dilbm_server_stats *stats) {
     }
     if (!s->running.empty()) {
         double t = s->now();
-        if (s->dirty || !s->batch) {
+        if (s->dirty || !has_batch(s)) {
             drop_batch(s);
-            s->members = s->running;
-            std::vector<dilbm_ctx *> m(s->members.size());
-            for (size_t q = 0; q < m.size(); ++q) m[q] = s->members[q]->ctx;
-            if ((rc = dilbm_batch_create(m.data(), (int)m.size(), nullptr, &s->batch))) return rc;
+            for (int c = 0; c < NSTORE; ++c) s->members[c].clear();
+            for (Job *j : s->running) s->members[j->grid.storage].push_back(j);
+            for (int c = 0; c < NSTORE; ++c) {
+                if (s->members[c].empty()) continue;
+                std::vector<dilbm_ctx *> m(s->members[c].size());
+                for (size_t q = 0; q < m.size(); ++q) m[q] = s->members[c][q]->ctx;
+                if ((rc = dilbm_batch_create(m.data(), (int)m.size(), nullptr, &s->batch[c]))) return rc;
+            }
             s->dirty = false;
         }
         // the macro-step ends where the first job finishes or opens its
         // mean-force window
         long long k = s->cfg.macro_steps;
-        for (Job *j : s->members) {
-            const long long left = j->nsteps - j->done;
-            k = std::min(k, left > j->window ? left - j->window : left);
-        }
-        if ((rc = dilbm_batch_step(s->batch, k))) return rc;
+        for (int c = 0; c < NSTORE; ++c)
+            for (Job *j : s->members[c]) {
+                const long long left = j->nsteps - j->done;
+                k = std::min(k, left > j->window ? left - j->window : left);
+            }
+        for (int c = 0; c < NSTORE; ++c)
+            if (s->batch[c] && (rc = dilbm_batch_step(s->batch[c], k))) return rc;
         double t2 = s->now();
         s->t_form += t2 - t;
         // newcomers are set up on their own streams while the GPU steps
         if ((rc = admit(s)) < 0) return rc;
         t = s->now();
         s->t_admit += t - t2;
-        std::vector<int> codes(s->members.size(), DILBM_OK);
-        if ((rc = dilbm_batch_errors(s->batch, codes.data()))) return rc;
+        std::vector<Job *> members;
+        std::vector<int> codes;
+        for (int c = 0; c < NSTORE; ++c) {
+            if (!s->batch[c]) continue;
+            std::vector<int> cc(s->members[c].size(), DILBM_OK);
+            if ((rc = dilbm_batch_errors(s->batch[c], cc.data()))) return rc;
+            members.insert(members.end(), s->members[c].begin(), s->members[c].end());
+            codes.insert(codes.end(), cc.begin(), cc.end());
+        }
         t2 = s->now();
         s->t_wait += t2 - t;
         ++s->macro;
         bool left = false;
-        for (size_t q = 0; q < s->members.size(); ++q) {
-            Job *j = s->members[q];
+        for (size_t q = 0; q < members.size(); ++q) {
+            Job *j = members[q];
             if (codes[q] != DILBM_OK) {
                 j->state = DILBM_JOB_FAILED;
                 j->error = codes[q];
@@ -312,7 +335,7 @@ int dilbm_server_progress(dilbm_server *s, dilbm_server_stats *stats) {
                 else release(s, j);
             }
             s->running.swap(still);
-            s->members.clear();
+            for (int c = 0; c < NSTORE; ++c) s->members[c].clear();
             s->dirty = true;
         }
         s->t_retire += s->now() - t2;

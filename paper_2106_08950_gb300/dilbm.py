@@ -28,6 +28,7 @@ MAX_CANDIDATES = 32
 
 FP32, FP16_DEV, BF16_DEV = 0, 1, 2
 STORAGE = {"fp32": FP32, "fp16": FP16_DEV, "bf16": BF16_DEV}
+STORAGE_PER_JOB = -1          # server: each job keeps its own storage
 SIDE = {W.PERIODIC: 0, W.VELOCITY: 1, W.PRESSURE: 2}
 
 
@@ -434,7 +435,8 @@ class Server:
                  memory_budget: float = 0.0, policy: int = ADMIT_FIFO):
         self.L = load_library()
         self.storage = storage
-        cfg = ServerConfig(STORAGE[storage], int(max_jobs), int(macro_steps), float(memory_budget), int(policy))
+        code = STORAGE_PER_JOB if storage == "per_job" else STORAGE[storage]
+        cfg = ServerConfig(code, int(max_jobs), int(macro_steps), float(memory_budget), int(policy))
         h = C.c_void_p()
         check(self.L.dilbm_server_create(C.byref(cfg), None, C.byref(h)))
         self.h = h
@@ -454,9 +456,13 @@ class Server:
     def clock(self) -> float:
         return float(self.L.dilbm_server_clock(self.h))
 
-    def submit(self, prob: W.Problem, nsteps: int, arrival: float = -1.0, mean_window: int = 0) -> int:
+    def submit(self, prob: W.Problem, nsteps: int, arrival: float = -1.0, mean_window: int = 0,
+               storage: Optional[str] = None) -> int:
+        """Queue a job; ``storage`` picks its storage on a "per_job" server
+        (default "fp32") and is ignored otherwise."""
         parts = make_particles(prob.particles)
-        job = Job(make_grid(prob, self.storage), prob.tau, prob.eps, C.cast(parts, C.POINTER(Particle)),
+        st = self.storage if self.storage != "per_job" else (storage or "fp32")
+        job = Job(make_grid(prob, st), prob.tau, prob.eps, C.cast(parts, C.POINTER(Particle)),
                   len(prob.particles), int(nsteps), int(mean_window), float(arrival))
         jid = C.c_longlong()
         check(self.L.dilbm_server_submit(self.h, C.byref(job), C.byref(jid)))

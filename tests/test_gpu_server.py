@@ -1,6 +1,7 @@
 """Serving (continuous batching): jobs that join and leave a running mix get
-bit for bit the result they get alone, admission respects the job slots and
-the memory budget, and a job that fails leaves the others untouched."""
+bit for bit the result they get alone (also when the mix holds jobs of
+different storage), admission respects the job slots and the memory budget,
+and a job that fails leaves the others untouched."""
 import numpy as np
 import pytest
 
@@ -72,6 +73,28 @@ def test_jobs_in_the_mix_match_alone_bitwise(stream, storage):
         Fa, Sa = alone(prob, n, storage, stream)
         assert np.array_equal(F, Fa), (jid, np.abs(F - Fa).max())
         assert np.array_equal(S, Sa), (jid, np.abs(S - Sa).max())
+    srv.close()
+
+
+def test_mixed_storage_jobs_match_alone_bitwise(stream):
+    # one server, jobs in FP32, FP16 and BF16 storage: one batch per storage
+    # type, all stepped by the same macro-steps; each job gets bit for bit the
+    # result it gets alone in its storage
+    jobs = small_jobs(38, 9)
+    kinds = ["fp32", "fp16", "bf16"]
+    srv = D.Server("per_job", max_jobs=16, macro_steps=16)
+    ids = []
+    for k, (p, n) in enumerate(jobs):
+        ids.append((srv.submit(p, n, storage=kinds[k % 3]), p, n, kinds[k % 3]))
+    seen = []
+    drain(srv, [], [], check=lambda st: seen.append(st.running))
+    assert max(seen) == len(jobs)
+    for jid, p, n, st in ids:
+        assert srv.status(jid).state == D.JOB_DONE
+        F, S = srv.result(jid)
+        Fa, Sa = alone(p, n, st, stream)
+        assert np.array_equal(F, Fa), (jid, st, np.abs(F - Fa).max())
+        assert np.array_equal(S, Sa), (jid, st)
     srv.close()
 
 
