@@ -203,7 +203,7 @@ def test_downscaled_periodic_suspension(stream):
 
 def test_full_size_periodic_suspension_sampled(stream):
     # The benchmark workload itself (4096^2, 2048 discs) for 6 steps in the
-    # same launch configuration; the oracle uses its 6-width phi cutoff.
+    # same launch configuration; the oracle uses the same 4-width phi cutoff.
     prob = W.periodic_suspension()
     o = O.OracleSim(prob, phi_cutoff=4 * prob.eps)
     g = D.Simulation(prob, stream=stream)

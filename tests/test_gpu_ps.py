@@ -153,6 +153,33 @@ def test_ps_larger_discs_arrive_mid_run(stream):
     assert ok, e
 
 
+def test_ps_full_size_suspension_sampled(stream):
+    # The benchmark workload (4096^2, 2048 discs) in PS-LBM for 2 steps, in
+    # the launch configuration bench.py times: every particle's force and
+    # state, 200k random nodes and the covered nodes, against the oracle.
+    prob = ps(W.periodic_suspension())
+    g = D.Simulation(prob, stream=stream)
+    o = O.OracleSim(prob)
+    g.step(2)
+    o.step(2)
+    g.sync()
+    fo = o.fields()
+    Fg, _, Sg = g.forces()
+    Fo, _, So = o.forces()
+    ok, e = PAR.compare_forces(Fg, Fo, PAR.TOL_FP32_SUSPENSION_FORCE, 12.0, atol=PAR.ps_force_floor(fo[3], So))
+    assert ok, e
+    ok, e = PAR.compare_state(Sg, So)
+    assert ok, e
+    gf = g.fields()
+    idx = np.random.default_rng(0).integers(0, prob.nx * prob.ny, size=200000)
+    ok, errs = PAR.compare_fields([a.ravel()[idx] for a in gf[:4]], [a.ravel()[idx] for a in fo[:4]])
+    assert ok, errs
+    covered = np.flatnonzero(fo[3].ravel() > 0)[::5]
+    ok, errs = PAR.compare_fields([a.ravel()[covered] for a in gf[:4]], [a.ravel()[covered] for a in fo[:4]])
+    assert ok, errs
+    assert np.abs(gf[3].ravel()[covered] - fo[3].ravel()[covered]).max() < 5e-6
+
+
 def test_ps_fp16_storage(stream):
     prob = ps(W.cylinder_drag())
     g, o = run_both(prob, 600, stream, storage="fp16")
