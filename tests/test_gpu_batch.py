@@ -99,3 +99,31 @@ def test_batch_rejects_mixed_storage(stream):
     with pytest.raises(D.DilbmError) as e:
         D.Batch([a, b])
     assert e.value.code == D.ERR_INVALID_ARG
+
+
+def test_full_size_batch_workload_against_oracle(stream):
+    # The benchmark's batch workload itself (64 uneven lattices, about 19 M
+    # nodes, 1-32 discs each), autotuned as bench.py does, for 4 steps: every
+    # member's forces and particle state, and 20k sampled nodes of each,
+    # against the oracle (same 4-width phi cutoff).
+    jobs = W.batch_lattices(seed=4)
+    members = [D.Simulation(j, stream=stream) for j in jobs]
+    batch = D.Batch(members)
+    batch.autotune(reps=2)
+    batch.step(4)
+    batch.sync()
+    rng = np.random.default_rng(1)
+    for k, (p, m) in enumerate(zip(jobs, members)):
+        o = O.OracleSim(p, phi_cutoff=4 * p.eps)
+        o.step(4)
+        Fg, _, Sg = m.forces()
+        Fo, _, So = o.forces()
+        ok, e = PAR.compare_forces(Fg, Fo, PAR.TOL_FP32_SUSPENSION_FORCE, max(q.r for q in p.particles))
+        assert ok, (k, p.name, e)
+        ok, e = PAR.compare_state(Sg, So)
+        assert ok, (k, p.name, e)
+        gf, of = m.fields(), o.fields()
+        idx = rng.integers(0, p.nx * p.ny, size=20000)
+        ok, errs = PAR.compare_fields([a.ravel()[idx] for a in gf[:4]], [a.ravel()[idx] for a in of[:4]])
+        assert ok, (k, p.name, errs)
+    batch.close()
