@@ -312,3 +312,60 @@ def test_reduced_precision_drag(stream, storage):
     err = abs(np.mean(fg) - np.mean(fo)) / abs(np.mean(fo))
     print(f"{storage} drag error {err:.3e} (instantaneous {abs(fg[-1] - fo[-1]) / abs(fo[-1]):.3e})")
     assert err <= PAR.TOL_REDUCED[storage]
+
+
+def test_lattice_past_32bit_offsets(stream):
+    # 16384^2 nodes in FP32: nine planes of 2^28 nodes, so population offsets
+    # pass 2^31; a moving, rotating disc near the far corner.  In 40 steps
+    # the disc and the nodes around it see only nodes within 40 of them, so
+    # they must match the same disc in a 256^2 periodic box (oracle), and a
+    # far node keeps the initial uniform flow.
+    import torch
+    n, off = 16384, (15872, 15972)
+    disc = dict(r=9.0, ux=0.02, uy=-0.01, omega=0.001, rho_s=1.3)
+    big = W.Problem(nx=n, ny=n, tau=0.8, eps=2.0, u0=(0.01, 0.004),
+                    particles=[W.Particle(128.3 + off[0], 128.7 + off[1], **disc)])
+    small = W.Problem(nx=256, ny=256, tau=0.8, eps=2.0, u0=(0.01, 0.004),
+                      particles=[W.Particle(128.3, 128.7, **disc)])
+    g = D.Simulation(big, stream=stream)
+    o = O.OracleSim(small)
+    g.step(40)
+    o.step(40)
+    g.sync()
+    Fg, _, Sg = g.forces()
+    Fo, _, So = o.forces()
+    ok, e = PAR.compare_forces(Fg, Fo, PAR.TOL_FP32_SUSPENSION_FORCE, 9.0)
+    assert ok, e
+    Sg = Sg.copy()
+    Sg[:, 0] -= off[0]
+    Sg[:, 1] -= off[1]
+    ok, e = PAR.compare_state(Sg, So)
+    assert ok, e
+    t = [torch.empty((n, n), dtype=torch.float32, device="cuda") for _ in range(4)]
+    g.fields_device(*t)
+    torch.cuda.synchronize()
+    block = [a[off[1] + 64:off[1] + 192, off[0] + 64:off[0] + 192].cpu().numpy() for a in t]
+    far = [float(a[100, 100]) for a in t]
+    del t
+    of = o.fields()
+    ok, errs = PAR.compare_fields(block, [a[64:192, 64:192] for a in of[:4]])
+    assert ok, errs
+    assert abs(far[1] - 0.01) < 1e-6 and abs(far[2] - 0.004) < 1e-6 and far[3] == 0.0
+    g.close()
+
+
+def test_zero_steps_change_nothing(stream):
+    prob = moving_particles()
+    g = D.Simulation(prob, stream=stream)
+    g.step(5)
+    f0 = g.populations()
+    F0, _, S0 = g.forces()
+    n0 = g.launches
+    g.step(0)
+    assert g.launches == n0
+    assert np.array_equal(g.populations(), f0)
+    F1, _, S1 = g.forces()
+    assert np.array_equal(F1, F0) and np.array_equal(S1, S0)
+    with pytest.raises(D.DilbmError):
+        g.step(-1)
+    g.close()
