@@ -435,7 +435,7 @@ void dilbm_server_destroy(dilbm_server *srv);
  *
  *   grid, tau, interface_width  as for dilbm_create; storage must be DILBM_FP32.
  *   f_in   device, DILBM_STATIC_POP_FLOATS(nx, ny) floats: the post-collision
- *          populations as deviations f_i - w_i (w_i the FP32 weights of Eq. 4),
+ *          populations as deviations f_i - w_i (w_i the D2Q9 weights in FP32),
  *          plane i of ny rows of DILBM_STATIC_PITCH(nx) floats, starting
  *          DILBM_STATIC_POP_OFFSET floats into the buffer; the
  *          DILBM_STATIC_POP_OFFSET floats before and after the planes must be
@@ -443,8 +443,13 @@ void dilbm_server_destroy(dilbm_server *srv);
  *   f_out  device, same size and layout, receives the next step's
  *          populations; must not alias f_in.
  *   particles, np  device array of np dilbm_particle, read and updated in
- *          place (np <= DILBM_STATIC_MAX_PARTICLES).
- *   force  device, np x 3 doubles: force and torque of this step (Eqs. 18-19).
+ *          place (np <= DILBM_STATIC_MAX_PARTICLES).  They are checked on the
+ *          device with dilbm_create's rules (centre inside the lattice, finite
+ *          positive radius and density, finite velocities, a phi tail of at
+ *          most 128 tiles); a bad particle gives DILBM_ERR_INVALID_ARG before
+ *          any other work, with f_out and the particles left unchanged.
+ *   force  device, np x 3 doubles: the hydrodynamic force (x, y) and torque
+ *          on each particle in this step.
  *   cuda_stream  stream for all work.
  * Limits: ceil(nx/128) * ceil(ny/8) <= DILBM_STATIC_MAX_TILES tiles and
  * np <= DILBM_STATIC_MAX_PARTICLES; larger problems are rejected with

@@ -102,10 +102,11 @@ int check_particles(const dilbm_grid *g, const dilbm_particle *p, int np) {
         const bool px = g->west.kind == DILBM_SIDE_PERIODIC, py = g->south.kind == DILBM_SIDE_PERIODIC;
         const bool inx = px ? (q.x >= 0.0 && q.x < g->nx) : (q.x >= 0.0 && q.x <= g->nx - 1);
         const bool iny = py ? (q.y >= 0.0 && q.y < g->ny) : (q.y >= 0.0 && q.y <= g->ny - 1);
-        if (!inx || !iny || !(q.r > 0.0) || !(q.rho_s > 0.0) || !std::isfinite(q.ux) ||
-            !std::isfinite(q.uy) || !std::isfinite(q.omega))
+        if (!inx || !iny || !(q.r > 0.0) || !(q.rho_s > 0.0) || !std::isfinite(q.r) || !std::isfinite(q.rho_s) ||
+            !std::isfinite(q.ux) || !std::isfinite(q.uy) || !std::isfinite(q.omega) || !std::isfinite(q.theta))
             return fail(DILBM_ERR_INVALID_ARG, "particle " + std::to_string(k) +
-                                                   " outside the lattice or with a non-positive radius/density");
+                                                   " outside the lattice, with a non-positive or non-finite "
+                                                   "radius/density, or with non-finite velocities");
     }
     return DILBM_OK;
 }

@@ -48,7 +48,7 @@ constexpr unsigned long long WAIT_LIMIT_NS = 1000000000ull;   // bounded device 
 
 enum : int { SIDE_PERIODIC = 0, SIDE_VELOCITY = 1, SIDE_PRESSURE = 2 };
 enum : int { WEST = 0, EAST = 1, SOUTH = 2, NORTH = 3 };
-enum : int { ERR_UNSTABLE = 1, ERR_OVERFLOW = 2, ERR_TIMEOUT = 4 };
+enum : int { ERR_UNSTABLE = 1, ERR_OVERFLOW = 2, ERR_TIMEOUT = 4, ERR_BADPARTICLE = 8 };
 
 // D2Q9 directions of Eq. 3 and weights of Eq. 4.
 __host__ __device__ constexpr int cxof(int i) { return i == 1 || i == 5 || i == 8 ? 1 : (i == 3 || i == 6 || i == 7 ? -1 : 0); }

@@ -24,6 +24,10 @@ namespace {
 // Limits of the static scratch (also stated in include/dilbm.h).
 constexpr int S_MAX_TILES = DILBM_STATIC_MAX_TILES;       // 128 x 8-node tiles
 constexpr int S_MAX_PARTICLES = DILBM_STATIC_MAX_PARTICLES;
+// The caller's population layout is the kernels' own: the header's offset is
+// the readable guard the bulk copies rely on, and its pitch is the kernels'.
+static_assert(GUARD == DILBM_STATIC_POP_OFFSET, "DILBM_STATIC_POP_OFFSET must equal the sweep's guard");
+static_assert(DILBM_STATIC_PITCH(1) == 32 && DILBM_STATIC_PITCH(33) == 64, "pitch: nx rounded up to 32");
 
 // Byte offsets of the scratch regions (each 256-byte aligned).
 constexpr size_t align256(size_t n) { return (n + 255) / 256 * 256; }
@@ -81,15 +85,29 @@ int scratch_address(unsigned char **out) {
     return DILBM_OK;
 }
 
-// dilbm_particle (array of structures, device) <-> the kernels' structure of arrays.
+// dilbm_particle (array of structures, device) <-> the kernels' structure of
+// arrays.  The particles live in device memory, so they are checked here, with
+// the same rules dilbm_create applies on the host: centre inside the lattice,
+// finite positive radius and density, finite velocities and angle, and a phi
+// tail that reaches at most MAXT tiles.  A bad particle sets ERR_BADPARTICLE,
+// and the host reads the error word before it launches anything else, so the
+// binning's minimum-image loops never see an out-of-range or non-finite centre.
 __global__ void particles_in_kernel(const dilbm_particle *__restrict__ in, Particles P, int np, int nx, int ny,
-                                    int per_x, int per_y, int *__restrict__ err) {
+                                    int per_x, int per_y, double cut_d, int *__restrict__ err) {
     const int p = blockIdx.x * blockDim.x + threadIdx.x;
     if (p >= np) return;
     const dilbm_particle q = in[p];
     const bool inx = per_x ? (q.x >= 0.0 && q.x < nx) : (q.x >= 0.0 && q.x <= nx - 1);
     const bool iny = per_y ? (q.y >= 0.0 && q.y < ny) : (q.y >= 0.0 && q.y <= ny - 1);
-    if (!inx || !iny || !(q.r > 0.0) || !(q.rho_s > 0.0)) atomicOr(err, 8);
+    const bool finite = isfinite(q.r) && isfinite(q.rho_s) && isfinite(q.ux) && isfinite(q.uy) &&
+                        isfinite(q.omega) && isfinite(q.theta);
+    bool ok = inx && iny && finite && q.r > 0.0 && q.rho_s > 0.0;
+    if (ok) {
+        const double R = q.r + cut_d;
+        const double tx = ceil((2.0 * R + 2.0) / TILE_W) + 1.0, ty = ceil((2.0 * R + 2.0) / TILE_H) + 1.0;
+        ok = tx * ty <= (double)MAXT;
+    }
+    if (!ok) atomicOr(err, ERR_BADPARTICLE);
     P.x[0][p] = q.x; P.y[0][p] = q.y; P.x[1][p] = q.x; P.y[1][p] = q.y;
     P.r[p] = q.r; P.ux[p] = q.ux; P.uy[p] = q.uy; P.omega[p] = q.omega; P.theta[p] = q.theta;
     P.rho_s[p] = q.rho_s; P.fixed[p] = q.fixed ? 1 : 0;
@@ -113,7 +131,8 @@ extern "C" int dilbm_step_static(const dilbm_grid *g, double tau, double interfa
     if (!g || !f_in || !f_out || f_in == f_out || (np > 0 && (!particles || !force)) || np < 0)
         return sfail(DILBM_ERR_INVALID_ARG, "dilbm_step_static: NULL or aliased buffer, or np < 0");
     if (g->storage != DILBM_FP32) return sfail(DILBM_ERR_INVALID_ARG, "dilbm_step_static: FP32 storage only");
-    if (g->nx < 3 || g->ny < 3 || !(tau > 0.5) || !(interface_width > 0.0))
+    if (g->nx < 3 || g->ny < 3 || !(tau > 0.5) || !std::isfinite(tau) || !(interface_width > 0.0) ||
+        !std::isfinite(interface_width))
         return sfail(DILBM_ERR_INVALID_ARG, "dilbm_step_static: nx, ny >= 3, tau > 0.5, interface width > 0");
     const dilbm_side *sides[4] = {&g->west, &g->east, &g->south, &g->north};
     for (int k = 0; k < 4; ++k)
@@ -133,7 +152,7 @@ extern "C" int dilbm_step_static(const dilbm_grid *g, double tau, double interfa
     Lattice L{};
     L.nx = g->nx;
     L.ny = g->ny;
-    L.pitch = (g->nx + 31) / 32 * 32;
+    L.pitch = DILBM_STATIC_PITCH(g->nx);
     L.plane = (long long)L.pitch * L.ny;
     L.ntx = (L.nx + TILE_W - 1) / TILE_W;
     L.nty = (L.ny + TILE_H - 1) / TILE_H;
@@ -222,8 +241,19 @@ extern "C" int dilbm_step_static(const dilbm_grid *g, double tau, double interfa
         return a;
     };
     if (np > 0) {
-        particles_in_kernel<<<(np + 127) / 128, 128, 0, st>>>(particles, P, np, L.nx, L.ny, L.per_x, L.per_y, err);
+        particles_in_kernel<<<(np + 127) / 128, 128, 0, st>>>(particles, P, np, L.nx, L.ny, L.per_x, L.per_y,
+                                                              ph.cut_d, err);
         S_CUDA(cudaGetLastError());
+        // nothing else runs on a bad particle: f_out and the caller's
+        // particles stay as they were
+        int h = 0;
+        S_CUDA(cudaMemcpyAsync(&h, err, sizeof(int), cudaMemcpyDeviceToHost, st));
+        S_CUDA(cudaStreamSynchronize(st));
+        if (h & ERR_BADPARTICLE)
+            return sfail(DILBM_ERR_INVALID_ARG, "dilbm_step_static: a particle lies outside the lattice, has a "
+                                                "non-finite or non-positive radius or density, non-finite "
+                                                "velocities, or a phi tail reaching more than " +
+                                                    std::to_string(MAXT) + " tiles; nothing was changed");
         // bin the particles where they are (positions copy 0, bins 0)
         particles_kernel<false><<<(np + PART_WARPS - 1) / PART_WARPS, PART_WARPS * 32, 0, st>>>(part_args(0, 0, 0, bins[0], bins[0]),
                                                                        nullptr, BatchIndex{});
@@ -272,7 +302,6 @@ extern "C" int dilbm_step_static(const dilbm_grid *g, double tau, double interfa
     int h = 0;
     S_CUDA(cudaMemcpyAsync(&h, err, sizeof(int), cudaMemcpyDeviceToHost, st));
     S_CUDA(cudaStreamSynchronize(st));
-    if (h & 8) return sfail(DILBM_ERR_INVALID_ARG, "dilbm_step_static: a particle lies outside the lattice or has r, rho_s <= 0");
     if (h & ERR_UNSTABLE) return sfail(DILBM_ERR_UNSTABLE, "a node reached rho <= 0 or a non-finite velocity");
     if (h & ERR_TIMEOUT) return sfail(DILBM_ERR_TIMEOUT, "a bounded device wait gave up (1 s)");
     if (h & ERR_OVERFLOW) return sfail(DILBM_ERR_OVERFLOW, "too many particles reach one lattice tile");

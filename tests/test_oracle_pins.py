@@ -253,6 +253,86 @@ def test_brute_force_phi_and_force_sums_tiny():
     assert np.allclose(F2, bF2, rtol=1e-11, atol=1e-16)
 
 
+def test_one_step_newton_euler_against_brute_force():
+    # Eqs. 22-24 for one step from the uniform state, with the force and
+    # torque recomputed here (pure Python, Eqs. 14, 18-19):
+    #   U1 = U0 + (F + (rho_s - rho_f) pi r^2 g) / m,  m = rho_s pi r^2,
+    #   omega1 = omega0 + T / I,  I = m r^2 / 2 (a disc of unit depth),
+    #   X1 = X0 + U1,  theta1 = theta0 + omega1  (symplectic Euler, dt = 1).
+    # A wrong moment of inertia (m r^2) or torque sign moves omega1 by
+    # |T / I| ~ 1e-4 relative, far above the 1e-12 bound.
+    g = (0.0, -1e-4)
+    p0 = W.Particle(5.3, 4.6, 2.7, ux=0.01, uy=-0.02, omega=0.003, theta=0.4, rho_s=1.2)
+    prob = W.Problem(nx=12, ny=10, tau=0.75, eps=1.5, u0=(0.012, 0.004), gravity=g, particles=[p0])
+    sim = O.OracleSim(prob)
+    sim.step(1)
+    _, _, st = sim.forces()
+    bphi, bown, rel = _brute_phi(prob, [p0])
+    one = np.ones((prob.ny, prob.nx))
+    F = _brute_forces(prob, [p0], one, prob.u0[0] * one, prob.u0[1] * one, bphi, bown, rel)[0]
+    assert abs(F[2]) > 1e-4 * abs(p0.omega) * 0.5 * p0.rho_s * math.pi * p0.r ** 4   # the torque matters
+    m = p0.rho_s * math.pi * p0.r ** 2
+    inertia = 0.5 * m * p0.r ** 2
+    u1 = p0.ux + (F[0] + (p0.rho_s - prob.rho_f) * math.pi * p0.r ** 2 * g[0]) / m
+    v1 = p0.uy + (F[1] + (p0.rho_s - prob.rho_f) * math.pi * p0.r ** 2 * g[1]) / m
+    w1 = p0.omega + F[2] / inertia
+    assert st[0, 3] == pytest.approx(u1, rel=1e-12, abs=1e-17)
+    assert st[0, 4] == pytest.approx(v1, rel=1e-12, abs=1e-17)
+    assert st[0, 5] == pytest.approx(w1, rel=1e-12, abs=1e-17)
+    assert st[0, 0] == pytest.approx(p0.x + u1, abs=1e-14)
+    assert st[0, 1] == pytest.approx(p0.y + v1, abs=1e-14)
+    assert st[0, 6] == pytest.approx(p0.theta + w1, abs=1e-14)
+    # the angular update differs from a moment of inertia m r^2 or a flipped
+    # torque by far more than the bound
+    assert abs(st[0, 5] - (p0.omega + F[2] / m / p0.r ** 2)) > 1e3 * 1e-12 * abs(w1)
+    assert abs(st[0, 5] - (p0.omega - F[2] / inertia)) > 1e3 * 1e-12 * abs(w1)
+
+
+@pytest.mark.parametrize("fm", [W.FORCE_EQ18, W.FORCE_MOMENTUM])
+def test_total_angular_momentum_invariant(fm):
+    # Lattice BGK keeps sum_x x cross j exactly: streaming moves c_i f_i from
+    # x to x + c_i, and (x + c_i) cross c_i = x cross c_i; the collision keeps
+    # each node's momentum.  The coupled collision hands node n the momentum
+    # m_n = phi rho (u_s - u*) (Eq. A.13), so the fluid gains sum x_n cross m_n;
+    # the particle receives T = -k sum (x_n - X) cross m_n (Eqs. 18-19) and
+    # F = -k sum m_n, and symplectic Euler gives its orbital part
+    # d(X cross M U) = X cross F.  Hence
+    #     k sum_x x cross j + I omega + X cross M U
+    # is invariant, with k = 1 - 1/2tau (Eq. 18 as printed) or 1 (momentum
+    # exchange), while the disturbance stays clear of the periodic edges: the
+    # box is larger than twice the steps plus the reach r + 4 eps about the
+    # disc.  A moment of inertia m r^2, a flipped torque or a dropped orbital
+    # term breaks it by orders of magnitude more than the bound.
+    steps = 30
+    n = 2 * (steps + 6 + 8) + 12
+    p0 = W.Particle(n / 2 + 0.3, n / 2 - 0.4, 6.0, ux=0.004, uy=-0.003, omega=0.01, rho_s=1.3)
+    prob = W.Problem(nx=n, ny=n, tau=0.7, eps=2.0, force_model=fm, particles=[p0])
+    k = (1.0 - 0.5 / prob.tau) if fm == W.FORCE_EQ18 else 1.0
+    sim = O.OracleSim(prob)
+    m = p0.rho_s * math.pi * p0.r ** 2
+    inertia = 0.5 * m * p0.r ** 2
+    ys, xs = np.mgrid[0:n, 0:n].astype(float)
+
+    def parts():
+        f = sim.populations()
+        jx = np.einsum("i,iyx->yx", C_LAT[:, 0], f)
+        jy = np.einsum("i,iyx->yx", C_LAT[:, 1], f)
+        lf = (xs * jy - ys * jx).sum()
+        _, _, st = sim.forces()
+        X, Y, U, V, om = st[0, 0], st[0, 1], st[0, 3], st[0, 4], st[0, 5]
+        return k * lf, inertia * om, m * (X * V - Y * U)
+
+    a0 = parts()
+    sim.step(steps)
+    a1 = parts()
+    assert abs(a1[1] - a0[1]) > 1e-3 * abs(a0[1])           # the disc's spin does change
+    assert abs(sum(a1) - sum(a0)) < 1e-12 * abs(a0[1])
+    # the readings a plausible slip would take instead
+    assert abs(a1[0] + 2 * a1[1] + a1[2] - (a0[0] + 2 * a0[1] + a0[2])) > 1e3 * 1e-12 * abs(a0[1])
+    assert abs(a1[0] - a1[1] + a1[2] - (a0[0] - a0[1] + a0[2])) > 1e3 * 1e-12 * abs(a0[1])
+    assert abs(a1[0] + a1[1] - (a0[0] + a0[1])) > 1e3 * 1e-12 * abs(a0[1])
+
+
 def test_translation_invariance():
     # An integer shift of every particle on a periodic box shifts the fields.
     prob = _moving_box()

@@ -115,3 +115,55 @@ def test_static_step_rejects_sizes_beyond_its_scratch():
     rc = L.dilbm_step_static(C.byref(grid), prob.tau, prob.eps, a.data_ptr(), b.data_ptr(), None, 0, None, None)
     assert rc == D.ERR_INVALID_ARG
     assert b"static scratch" in L.dilbm_last_error()
+
+
+@pytest.mark.parametrize("bad", ["x_left_of_wall", "zero_radius", "nan_velocity", "inf_x_periodic",
+                                 "huge_x_periodic", "huge_radius"])
+def test_static_step_rejects_bad_particles_and_changes_nothing(bad):
+    # The particles sit in device memory, so the entry point checks them on
+    # the device before anything else runs: a bad one is reported as
+    # INVALID_ARG, and the output populations and the particles are untouched.
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    L = D.load_library()
+    L.dilbm_step_static.argtypes = [C.POINTER(D.Grid), C.c_double, C.c_double, C.c_void_p, C.c_void_p,
+                                    C.c_void_p, C.c_int, C.c_void_p, C.c_void_p]
+    L.dilbm_step_static.restype = C.c_int
+    good = W.Particle(20.3, 12.7, 6.0, ux=0.02, uy=0.01, omega=0.002, rho_s=1.3)
+    if bad in ("inf_x_periodic", "huge_x_periodic"):
+        prob = W.Problem(nx=160, ny=40, tau=0.7, eps=2.0, particles=[good])
+    else:
+        prob = W.sedimentation(nx=64, ny=96, r=6.0, rho_s=1.5, g=2e-5, x0=30.0, y0=60.0)
+    q = W.Particle(30.0, 20.0, 5.0, rho_s=1.2)
+    if bad == "x_left_of_wall":
+        q.x = -3.0
+    elif bad == "zero_radius":
+        q.r = 0.0
+    elif bad == "nan_velocity":
+        q.ux = float("nan")
+    elif bad == "inf_x_periodic":
+        q.x = float("inf")
+    elif bad == "huge_x_periodic":
+        q.x = 1e17
+    else:
+        q.r = 1e4
+    parts_in = list(prob.particles) + [q]
+    npart, nx, ny = len(parts_in), prob.nx, prob.ny
+    n = 9 * ny * pitch_of(nx) + 2 * POP_OFFSET
+    fa = torch.zeros(n, dtype=torch.float32, device="cuda")
+    fb = torch.full((n,), 7.0, dtype=torch.float32, device="cuda")
+    raw = bytes(D.make_particles(parts_in))
+    pdev = torch.from_numpy(np.frombuffer(raw, dtype=np.uint8).copy()).cuda()
+    force = torch.zeros(npart * 3, dtype=torch.float64, device="cuda")
+    grid = D.make_grid(prob, "fp32")
+    stream = torch.cuda.Stream()
+    torch.cuda.synchronize()
+    rc = L.dilbm_step_static(C.byref(grid), prob.tau, prob.eps, fa.data_ptr(), fb.data_ptr(),
+                             pdev.data_ptr(), npart, force.data_ptr(), int(stream.cuda_stream))
+    torch.cuda.synchronize()
+    assert rc == D.ERR_INVALID_ARG, (rc, L.dilbm_last_error())
+    assert b"nothing was changed" in L.dilbm_last_error()
+    assert bytes(pdev.cpu().numpy().tobytes()) == raw
+    assert bool((fb == 7.0).all())
+    assert bool((force == 0.0).all())
