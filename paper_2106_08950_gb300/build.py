@@ -50,7 +50,10 @@ def build(force: bool = False, verbose: bool = False) -> str:
             return LIB
         objdir = os.path.join(PKG, "_build")
         os.makedirs(objdir, exist_ok=True)
-        common = [nvcc(), *ARCH, "-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC",
+        # -fmad=false: a multiply and an add are fused only where the source
+        # says so (fmaf and the paired intrinsics), so every instantiation of a
+        # kernel (each launch shape, batched or not) rounds alike
+        common = [nvcc(), *ARCH, "-O3", "-lineinfo", "-std=c++17", "-fmad=false", "-Xcompiler", "-fPIC",
                   "-I", INCLUDE, "-I", CSRC, "--expt-relaxed-constexpr"]
         procs, objs = [], []
         for src in sources():

@@ -20,10 +20,13 @@
 //
 // The sweep is a persistent kernel: each warp walks row segments of 128 nodes
 // and streams every segment's nine source rows (plus a 16-byte halo on each
-// side) into a two-stage shared-memory ring with bulk asynchronous copies
-// (cp.async.bulk, completion on an mbarrier), so the next segment's loads are
-// in flight while the current one is collided.  Writes go straight from
-// registers as 16-byte stores.
+// side) into shared memory with bulk asynchronous copies (cp.async.bulk,
+// completion on an mbarrier); once a segment's rows have been read, the copy
+// of the warp's next segment is issued into the same buffer, so it is in
+// flight while the current segment is collided.  Each lane sweeps its four
+// nodes as two pairs (nodes 2l, 2l + 1 of each half segment), which keeps
+// few registers live; writes go straight from registers, one contiguous run
+// per plane and pair.
 #pragma once
 
 #include <cuda_bf16.h>
@@ -36,17 +39,17 @@ namespace dilbm {
 
 constexpr int TILE_W = 128;   // nodes per row segment (32 lanes x 4 nodes) and per tile row
 constexpr int TILE_H = 8;     // rows per binning tile
-constexpr int VEC = 4;        // nodes per thread
 constexpr int MAXC = 32;      // candidate particles per tile
 constexpr int MAXT = 128;     // tiles one particle's phi tail may reach
 constexpr int NREC = 3;       // float4 records per binned particle
-constexpr int STAGES = 2;     // shared-memory ring depth per warp
+constexpr int STAGES = 1;     // row segments staged ahead per warp (shared-memory ring depth)
 constexpr int SWEEP_WARPS = 8;   // default rows in flight per block (one row segment per warp)
 constexpr int GUARD = 256;    // elements kept readable before and after a population buffer
 constexpr float PHI_CUT_WIDTHS = 4.0f;   // phi tail kept up to 4 interface widths (phi > 1.1e-7)
 constexpr unsigned long long WAIT_LIMIT_NS = 1000000000ull;   // bounded device waits: 1 s
 
-enum : int { SIDE_PERIODIC = 0, SIDE_VELOCITY = 1, SIDE_PRESSURE = 2 };
+enum : int { SIDE_PERIODIC = 0, SIDE_VELOCITY = 1, SIDE_PRESSURE = 2,
+             SIDE_HALO = 3 };   // a strip's cut: the rows beyond it come from halo buffers
 enum : int { WEST = 0, EAST = 1, SOUTH = 2, NORTH = 3 };
 enum : int { ERR_UNSTABLE = 1, ERR_OVERFLOW = 2, ERR_TIMEOUT = 4, ERR_BADPARTICLE = 8 };
 
@@ -59,52 +62,31 @@ __host__ __device__ constexpr float wof(int i) { return i == 0 ? 4.0f / 9.0f : (
 template <typename T> struct Storage;
 
 template <> struct Storage<float> {
-    static __device__ __forceinline__ float4 load4(const float *p) { return __ldg(reinterpret_cast<const float4 *>(p)); }
-    static __device__ __forceinline__ float4 lds4(const float *p) { return *reinterpret_cast<const float4 *>(p); }
     static __device__ __forceinline__ float load1(const float *p) { return __ldg(p); }
     static __device__ __forceinline__ float lds1(const float *p) { return *p; }
-    static __device__ __forceinline__ void store4(float *p, float4 v) { *reinterpret_cast<float4 *>(p) = v; }
     static __device__ __forceinline__ void store1(float *p, float v) { *p = v; }
+    static __device__ __forceinline__ float2 lds2(const float *p) { return *reinterpret_cast<const float2 *>(p); }
+    static __device__ __forceinline__ void store2(float *p, float2 v) { *reinterpret_cast<float2 *>(p) = v; }
 };
 
 template <> struct Storage<__half> {
-    static __device__ __forceinline__ float4 cvt(uint2 u) {
-        __half2 a = *reinterpret_cast<__half2 *>(&u.x), b = *reinterpret_cast<__half2 *>(&u.y);
-        float2 fa = __half22float2(a), fb = __half22float2(b);
-        return make_float4(fa.x, fa.y, fb.x, fb.y);
-    }
-    static __device__ __forceinline__ float4 load4(const __half *p) { return cvt(__ldg(reinterpret_cast<const uint2 *>(p))); }
-    static __device__ __forceinline__ float4 lds4(const __half *p) { return cvt(*reinterpret_cast<const uint2 *>(p)); }
     static __device__ __forceinline__ float load1(const __half *p) { return __half2float(__ldg(p)); }
     static __device__ __forceinline__ float lds1(const __half *p) { return __half2float(*p); }
-    static __device__ __forceinline__ void store4(__half *p, float4 v) {
-        __half2 a = __floats2half2_rn(v.x, v.y), b = __floats2half2_rn(v.z, v.w);
-        uint2 u;
-        u.x = *reinterpret_cast<uint32_t *>(&a);
-        u.y = *reinterpret_cast<uint32_t *>(&b);
-        *reinterpret_cast<uint2 *>(p) = u;
-    }
     static __device__ __forceinline__ void store1(__half *p, float v) { *p = __float2half_rn(v); }
+    static __device__ __forceinline__ float2 lds2(const __half *p) { return __half22float2(*reinterpret_cast<const __half2 *>(p)); }
+    static __device__ __forceinline__ void store2(__half *p, float2 v) { *reinterpret_cast<__half2 *>(p) = __floats2half2_rn(v.x, v.y); }
 };
 
 template <> struct Storage<__nv_bfloat16> {
-    static __device__ __forceinline__ float4 cvt(uint2 u) {
-        __nv_bfloat162 a = *reinterpret_cast<__nv_bfloat162 *>(&u.x), b = *reinterpret_cast<__nv_bfloat162 *>(&u.y);
-        float2 fa = __bfloat1622float2(a), fb = __bfloat1622float2(b);
-        return make_float4(fa.x, fa.y, fb.x, fb.y);
-    }
-    static __device__ __forceinline__ float4 load4(const __nv_bfloat16 *p) { return cvt(__ldg(reinterpret_cast<const uint2 *>(p))); }
-    static __device__ __forceinline__ float4 lds4(const __nv_bfloat16 *p) { return cvt(*reinterpret_cast<const uint2 *>(p)); }
     static __device__ __forceinline__ float load1(const __nv_bfloat16 *p) { return __bfloat162float(__ldg(p)); }
     static __device__ __forceinline__ float lds1(const __nv_bfloat16 *p) { return __bfloat162float(*p); }
-    static __device__ __forceinline__ void store4(__nv_bfloat16 *p, float4 v) {
-        __nv_bfloat162 a = __floats2bfloat162_rn(v.x, v.y), b = __floats2bfloat162_rn(v.z, v.w);
-        uint2 u;
-        u.x = *reinterpret_cast<uint32_t *>(&a);
-        u.y = *reinterpret_cast<uint32_t *>(&b);
-        *reinterpret_cast<uint2 *>(p) = u;
-    }
     static __device__ __forceinline__ void store1(__nv_bfloat16 *p, float v) { *p = __float2bfloat16_rn(v); }
+    static __device__ __forceinline__ float2 lds2(const __nv_bfloat16 *p) {
+        return __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162 *>(p));
+    }
+    static __device__ __forceinline__ void store2(__nv_bfloat16 *p, float2 v) {
+        *reinterpret_cast<__nv_bfloat162 *>(p) = __floats2bfloat162_rn(v.x, v.y);
+    }
 };
 
 // Elements in the 16-byte halo on each side of a staged row segment, and the
@@ -145,9 +127,28 @@ struct Lattice {
     // f^eq(rho_init, u0) and q a power of two that keeps small s_i out of
     // the FP16 subnormals.  FP32 storage holds d_i itself.
     float ref_e[9];             // e_i
-    float ref_ne[9];            // -e_i / q
     float ref_q, ref_iq;        // q, 1 / q
+    // The moments of the reference e_i (it is the equilibrium deviation of
+    // Eq. 2 at rho_init, u0): m0 = rho_init - 1, B = rho_init u0,
+    // M = rho_init u0 u0^T (xx, yy, xy), in the moment form below.  The
+    // 16-bit sweep takes moments of the stored s_i and adds these, so no
+    // per-direction offset enters its inner loop.
+    float ref_m[6];
+    // A strip of a larger lattice (one rank's rows): the post-collision rows
+    // just south (halo[0]) and north (halo[1]) of it, 9 plane rows of `pitch`
+    // elements each, with GUARD readable elements before and after; NULL
+    // where the side is a physical side of the lattice.
+    const void *halo[2];
 };
+
+// Is row y of the lattice a south / north edge row (a physical side, not a
+// periodic axis and not a strip's cut)?
+__host__ __device__ inline bool south_edge_row(const Lattice &L, int y) {
+    return !L.per_y && y == 0 && L.side_kind[SOUTH] != SIDE_HALO;
+}
+__host__ __device__ inline bool north_edge_row(const Lattice &L, int y) {
+    return !L.per_y && y == L.ny - 1 && L.side_kind[NORTH] != SIDE_HALO;
+}
 
 // Stored value <-> FP32 deviation d_i for direction i (exact scalings by a
 // power of two, one rounding in the offset).
@@ -157,27 +158,8 @@ template <typename T> __device__ __forceinline__ float from_store(const Lattice 
 }
 template <typename T> __device__ __forceinline__ float to_store(const Lattice &L, int i, float d) {
     if constexpr (std::is_same<T, float>::value) return d;
-    else return fmaf(d, L.ref_iq, L.ref_ne[i]);
+    else return (d - L.ref_e[i]) * L.ref_iq;       // (one rounding: the scaling is exact)
 }
-template <typename T> __device__ __forceinline__ float4 from_store4(const Lattice &L, int i, float4 v) {
-    if constexpr (std::is_same<T, float>::value) {
-        return v;
-    } else {
-        const float2 q = make_float2(L.ref_q, L.ref_q), e = make_float2(L.ref_e[i], L.ref_e[i]);
-        const float2 a = __ffma2_rn(make_float2(v.x, v.y), q, e), b = __ffma2_rn(make_float2(v.z, v.w), q, e);
-        return make_float4(a.x, a.y, b.x, b.y);
-    }
-}
-template <typename T> __device__ __forceinline__ float4 to_store4(const Lattice &L, int i, float4 d) {
-    if constexpr (std::is_same<T, float>::value) {
-        return d;
-    } else {
-        const float2 q = make_float2(L.ref_iq, L.ref_iq), e = make_float2(L.ref_ne[i], L.ref_ne[i]);
-        const float2 a = __ffma2_rn(make_float2(d.x, d.y), q, e), b = __ffma2_rn(make_float2(d.z, d.w), q, e);
-        return make_float4(a.x, a.y, b.x, b.y);
-    }
-}
-
 struct Physics {
     float omega;                // 1 / tau
     float kf;                   // 1 - 1/(2 tau): prefactor of F_i (Eq. 15)
@@ -206,6 +188,16 @@ __device__ __forceinline__ int wrap_or_clamp(int v, int n, int periodic) {
     return v < 0 ? 0 : (v >= n ? n - 1 : v);
 }
 
+// Row sy (in [-1, ny]) of plane i of the post-collision populations `src`:
+// wrapped on a periodic axis, from a halo buffer across a strip's cut, else
+// clamped (an edge row, whose pulled values the edge scheme replaces).
+template <typename T>
+__device__ __forceinline__ const T *plane_row(const T *src, const Lattice &L, int i, int sy) {
+    if (sy < 0 && L.halo[0]) return static_cast<const T *>(L.halo[0]) + (long long)i * L.pitch;
+    if (sy >= L.ny && L.halo[1]) return static_cast<const T *>(L.halo[1]) + (long long)i * L.pitch;
+    return src + i * L.plane + (long long)wrap_or_clamp(sy, L.ny, L.per_y) * L.pitch;
+}
+
 // Populations of the form X_i = w_i [S + 3 c_i.B + 4.5 c_i^T M c_i] (the
 // equilibrium of Eq. 2 has this form with B = rho u, M = rho u u^T; so has the
 // collision's relaxation target plus force term of Eqs. 13 and 15), for a
@@ -221,13 +213,13 @@ constexpr float A1F = 1.0f / 3.0f;
 constexpr float A5F = (float)((1.0 - 2.0 * (double)A1F) / 4.0);
 
 __device__ __forceinline__ void moment_form(float m0, float Bx, float By, float Mxx, float Myy, float Mxy, float X[9]) {
-    const float S = m0 - 1.5f * (Mxx + Myy);
+    const float S = fmaf(-1.5f, Mxx + Myy, m0);
     const float ax = fmaf(W1F, S, 0.5f * Mxx), ay = fmaf(W1F, S, 0.5f * Myy);
     const float tr = Mxx + Myy;
     const float ap = fmaf(W5F, S, 0.125f * fmaf(2.0f, Mxy, tr));
     const float am = fmaf(W5F, S, 0.125f * fmaf(-2.0f, Mxy, tr));
     const float bx = A1F * Bx, by = A1F * By, bp = A5F * (Bx + By), bm = A5F * (By - Bx);
-    X[0] = m0 - 2.0f * ((ax + ay) + (ap + am));
+    X[0] = fmaf(-2.0f, (ax + ay) + (ap + am), m0);
     X[1] = ax + bx; X[3] = ax - bx;
     X[2] = ay + by; X[4] = ay - by;
     X[5] = ap + bp; X[7] = ap - bp;
@@ -283,30 +275,60 @@ __device__ __forceinline__ void relax2(float2 d[9], float omega, const float2 X[
     for (int i = 0; i < 9; ++i) d[i] = add2(d[i], fma2(f2(-omega), d[i], X[i]));
 }
 
-// phi = 0 (plain BGK of Eq. 1): B = omega j and, as rho u = j,
-// M = omega rho u u^T = B u^T.
-__device__ __forceinline__ void collide_plain2(float2 d[9], float omega, float2 drho, float2 jx, float2 jy,
-                                               float2 ux, float2 uy) {
+// The collision acts on the stored values.  FP32 stores d_i itself.  16-bit
+// storage holds s_i = (d_i - e_i) / q, and since e_i has the moment form
+// with the reference moments (m0e, Be, Me) and q is a power of two,
+//   s'_i = s_i + (Y_i - omega s_i),  Y = (X - omega e) / q,
+// where Y is the moment form of (omega sum s, (B - omega Be) / q,
+// (M - omega Me) / q): the zeroth input is omega times the stored values'
+// own sum, the first moment's part omega j becomes omega times the stored
+// first moment, and only M, a product of the physical moments, needs the
+// reference subtracted.  (ms, jxs, jys are the moments of the stored values.)
+template <typename T>
+__device__ __forceinline__ void relax_to2(float2 d[9], const Lattice &L, float omega, float2 ms, float2 Bxs,
+                                          float2 Bys, float2 Mxx, float2 Myy, float2 Mxy) {
     const float2 om = f2(omega);
-    const float2 Bx = mul2(om, jx), By = mul2(om, jy);
+    if constexpr (!std::is_same<T, float>::value) {
+        const float2 iq = f2(L.ref_iq);
+        Mxx = mul2(sub2(Mxx, f2(omega * L.ref_m[3])), iq);
+        Myy = mul2(sub2(Myy, f2(omega * L.ref_m[4])), iq);
+        Mxy = mul2(sub2(Mxy, f2(omega * L.ref_m[5])), iq);
+    }
     float2 X[9];
-    moment_form2(mul2(om, drho), Bx, By, mul2(Bx, ux), mul2(By, uy), mul2(Bx, uy), X);
+    moment_form2(mul2(om, ms), Bxs, Bys, Mxx, Myy, Mxy, X);
     relax2(d, omega, X);
 }
 
-__device__ __forceinline__ void collide2(float2 d[9], float omega, float2 drho, float2 rho, float2 jx, float2 jy,
-                                         float2 ux, float2 uy, float2 kphi, float2 prho, float2 dux, float2 duy,
-                                         float2 usx, float2 usy, float2 uax, float2 uay) {
+// phi = 0 (plain BGK of Eq. 1): B = omega j and, as rho u = j,
+// M = omega rho u u^T = B u^T.
+template <typename T>
+__device__ __forceinline__ void collide_plain2(float2 d[9], const Lattice &L, float omega, float2 ms, float2 jxs,
+                                               float2 jys, float2 jx, float2 jy, float2 ux, float2 uy) {
+    const float2 om = f2(omega);
+    const float2 Bx = mul2(om, jx), By = mul2(om, jy);
+    if constexpr (std::is_same<T, float>::value)
+        relax_to2<T>(d, L, omega, ms, Bx, By, mul2(Bx, ux), mul2(By, uy), mul2(Bx, uy));
+    else
+        relax_to2<T>(d, L, omega, ms, mul2(om, jxs), mul2(om, jys), mul2(Bx, ux), mul2(By, uy), mul2(Bx, uy));
+}
+
+template <typename T>
+__device__ __forceinline__ void collide2(float2 d[9], const Lattice &L, float omega, float2 ms, float2 jxs,
+                                         float2 jys, float2 rho, float2 ux, float2 uy, float2 kphi, float2 prho,
+                                         float2 dux, float2 duy, float2 usx, float2 usy, float2 uax, float2 uay) {
     const float2 om = f2(omega);
     const float2 orho = mul2(om, rho);
-    const float2 Bx = fma2(om, jx, mul2(prho, dux)), By = fma2(om, jy, mul2(prho, duy));
+    float2 px = mul2(prho, dux), py = mul2(prho, duy);
+    if constexpr (!std::is_same<T, float>::value) {
+        px = mul2(px, f2(L.ref_iq));
+        py = mul2(py, f2(L.ref_iq));
+    }
+    const float2 Bxs = fma2(om, jxs, px), Bys = fma2(om, jys, py);
     const float2 rux = mul2(orho, ux);
     const float2 Mxx = fma2(rux, ux, mul2(kphi, mul2(dux, add2(usx, uax))));
     const float2 Myy = fma2(mul2(orho, uy), uy, mul2(kphi, mul2(duy, add2(usy, uay))));
     const float2 Mxy = fma2(rux, uy, mul2(kphi, fma2(dux, usy, mul2(uax, duy))));
-    float2 X[9];
-    moment_form2(mul2(om, drho), Bx, By, Mxx, Myy, Mxy, X);
-    relax2(d, omega, X);
+    relax_to2<T>(d, L, omega, ms, Bxs, Bys, Mxx, Myy, Mxy);
 }
 
 // Tile ranges along one axis covered by [X - R, X + R] (a disc's bounding
@@ -403,8 +425,7 @@ __device__ __forceinline__ void issue_segment(const T *__restrict__ src, const L
     if (lane == 0) mbar_expect_tx(bar, 9u * SW * sizeof(T));
     __syncwarp();
     if (lane < 9) {
-        const int sy = wrap_or_clamp(y - cyof(lane), L.ny, L.per_y);
-        const T *g = src + lane * L.plane + (long long)sy * L.pitch + (tx * TILE_W - H);
+        const T *g = plane_row<T>(src, L, lane, y - cyof(lane)) + (tx * TILE_W - H);
         bulk_copy_g2s(stage + lane * SW, g, SW * sizeof(T), bar);
     }
 }
@@ -414,8 +435,7 @@ __device__ __forceinline__ void pull_node_scalar(const T *__restrict__ src, cons
 #pragma unroll
     for (int i = 0; i < 9; ++i) {
         int sx = wrap_or_clamp(x - cxof(i), L.nx, L.per_x);
-        int sy = wrap_or_clamp(y - cyof(i), L.ny, L.per_y);
-        d[i] = from_store<T>(L, i, Storage<T>::load1(src + i * L.plane + (long long)sy * L.pitch + sx));
+        d[i] = from_store<T>(L, i, Storage<T>::load1(plane_row<T>(src, L, i, y - cyof(i)) + sx));
     }
 }
 
@@ -451,11 +471,21 @@ __device__ __forceinline__ void extrapolate(const Lattice &L, int side, const fl
     } else {
         drb = sdr; ubx = unx; uby = uny;
     }
-    float eb[9], en[9];
-    eq_dev9(drb, 1.0f + drb, ubx, uby, eb);
-    eq_dev9(drn, rhon, unx, uny, en);
+    // f^eq(rho_b, u_b) - f^eq(rho_n, u_n) is linear in the moments, so it is
+    // the moment form of the moment differences, formed without cancellation:
+    // with d = rho_b - rho_n and v = u_b - u_n,
+    //   rho_b u_b - rho_n u_n = d u_b + rho_n v,
+    //   rho_b u_b u_b - rho_n u_n u_n = d u_b u_b + rho_n (v (u_b + u_n))   (xx, yy),
+    //   rho_b ubx uby - rho_n unx uny = d ubx uby + rho_n (vx uby + unx vy).
+    const float d = drb - drn, vx = ubx - unx, vy = uby - uny;
+    const float Bx = fmaf(d, ubx, rhon * vx), By = fmaf(d, uby, rhon * vy);
+    const float Mxx = fmaf(d * ubx, ubx, rhon * (vx * (ubx + unx)));
+    const float Myy = fmaf(d * uby, uby, rhon * (vy * (uby + uny)));
+    const float Mxy = fmaf(d * ubx, uby, rhon * fmaf(vx, uby, unx * vy));
+    float X[9];
+    moment_form(d, Bx, By, Mxx, Myy, Mxy, X);
 #pragma unroll
-    for (int i = 0; i < 9; ++i) out[i] = eb[i] + (dn[i] - en[i]);
+    for (int i = 0; i < 9; ++i) out[i] = dn[i] + X[i];
 }
 
 // An edge node whose inner neighbour lies on another row (south / north
@@ -463,7 +493,7 @@ __device__ __forceinline__ void extrapolate(const Lattice &L, int side, const fl
 template <typename T>
 __device__ __noinline__ Pop9 edge_values(const T *__restrict__ src, const Lattice &L, int x, int y) {
     const int onx = !L.per_x && (x == 0 || x == L.nx - 1);
-    const int ony = !L.per_y && (y == 0 || y == L.ny - 1);
+    const int ony = south_edge_row(L, y) || north_edge_row(L, y);
     const int side = ony ? (y == 0 ? SOUTH : NORTH) : (x == 0 ? WEST : EAST);
     const int xn = onx ? (x == 0 ? 1 : L.nx - 2) : x;
     const int yn = ony ? (y == 0 ? 1 : L.ny - 2) : y;
@@ -627,7 +657,7 @@ struct SweepArgs {
 // held in the kernel's parameter space (uniform constant-cache reads, no
 // aliasing with the stores): lattice k owns row segments
 // [item_start[k], item_start[k+1]) and tiles [tile_start[k], tile_start[k+1]).
-constexpr int BATCH_LAUNCH_MAX = 88;     // lattices per batched launch
+constexpr int BATCH_LAUNCH_MAX = 84;     // lattices per batched launch
 
 template <typename T>
 struct BatchArgs {
@@ -664,10 +694,29 @@ struct Ring {
     uint32_t pending;           // bit s: stage s has copies in flight
 };
 
+// The streamed value f_i(x) = f'_i(x - c_i) of plane i at node e of the
+// staged segment (e in [-1, TILE_W]: the 16-byte halos hold the neighbours).
+template <typename T, int I>
+__device__ __forceinline__ float staged_pull(const Lattice &L, const T *stage, int e) {
+    constexpr int H = halo_of<T>(), SW = segw_of<T>();
+    return from_store<T>(L, I, Storage<T>::lds1(stage + I * SW + H + e - cxof(I)));
+}
+
+template <typename T, int I = 0>
+__device__ __forceinline__ void staged_pull9(const Lattice &L, const T *stage, int e, float out[9]) {
+    out[I] = staged_pull<T, I>(L, stage, e);
+    if constexpr (I < 8) staged_pull9<T, I + 1>(L, stage, e, out);
+}
+
+// Slot m (0 or 1) of a node pair.
+__device__ __forceinline__ float &slot(float2 &v, int m) { return m ? v.y : v.x; }
+
 // One row segment (row y, segment tx) of lattice A: wait for its staged rows,
-// hand the stage to the segment `nxt` (row ny2, segment nx2 of lattice An)
-// when there is one, then stream, collide, store and sum the segment's
-// force / torque.  Returns false if the bounded wait gave up.
+// then sweep its 128 nodes in two passes of 64 (lane l takes nodes 2l and
+// 2l + 1 of each half, so every store of a pass is one contiguous run per
+// plane), hand the stage to the segment `nxt` (row ny2, segment nx2 of
+// lattice An) once the second pass has read it, and sum the segment's force /
+// torque per candidate particle.  Returns false if the bounded wait gave up.
 template <typename T, int MODE, bool EDGES, bool PS = false>
 __device__ __forceinline__ bool sweep_segment(const SweepArgs<T> &A, int y, int tx, T *stage, Ring &ring, int s,
                                               bool has_next, const SweepArgs<T> &An, int ny2, int nx2,
@@ -677,7 +726,6 @@ __device__ __forceinline__ bool sweep_segment(const SweepArgs<T> &A, int y, int 
     const Physics &ph = A.ph;
     const int ty = y / TILE_H, tile = ty * L.ntx + tx;
     const int tx0 = tx * TILE_W, ty0 = ty * TILE_H;
-    const int x0 = tx0 + lane * VEC;
 
     // ---- the tile's candidate particles (records written by the binning),
     // loaded before the wait so that their latency overlaps it
@@ -694,209 +742,187 @@ __device__ __forceinline__ bool sweep_segment(const SweepArgs<T> &A, int y, int 
         }
     }
 
-    // ---- wait for the staged rows and tile header
+    // ---- wait for the staged rows
     // a warp-uniform decision: every lane leaves together if any gave up
     if (!__all_sync(0xffffffffu, mbar_wait_bounded(&ring.bars[s], (ring.parity >> s) & 1u))) return false;
     ring.parity ^= 1u << s;
     ring.pending &= ~(1u << s);
 
-    // ---- pull-stream from the staged rows: f_i(x, t+1) = f'_i(x - c_i, t)
-    const int c0 = H + lane * VEC;
-    float d[9][VEC];
-#pragma unroll
-    for (int i = 0; i < 9; ++i) {
-        float4 v = Storage<T>::lds4(stage + i * SW + c0);
-        if (cxof(i) == 1) v = make_float4(Storage<T>::lds1(stage + i * SW + c0 - 1), v.x, v.y, v.z);
-        else if (cxof(i) == -1) v = make_float4(v.y, v.z, v.w, Storage<T>::lds1(stage + i * SW + c0 + VEC));
-        v = from_store4<T>(L, i, v);
-        d[i][0] = v.x; d[i][1] = v.y; d[i][2] = v.z; d[i][3] = v.w;
-    }
-    const bool row_edge = EDGES && !L.per_y && (y == 0 || y == L.ny - 1);
+    const bool row_edge = EDGES && (south_edge_row(L, y) || north_edge_row(L, y));
     const bool col_edge = EDGES && !L.per_x && (tx == 0 || tx0 + TILE_W >= L.nx);
-    // an east edge that opens its segment (nx = 1 mod 128, lane 0) has its
-    // inner neighbour in the previous segment: pull that neighbour's values
-    // from the staged halo before the stage is recycled, into the slot of
-    // node x0 + 1, which lies past the edge and is never stored
-    if (col_edge && !row_edge && lane == 0 && x0 == L.nx - 1) {
-#pragma unroll
-        for (int i = 0; i < 9; ++i)
-            d[i][1] = from_store<T>(L, i, Storage<T>::lds1(stage + i * SW + (c0 - 1 - cxof(i))));
-    }
-    __syncwarp();
-    // recycle the stage for the segment STAGES items ahead
-    if (has_next) {
-        fence_proxy_async_smem();
-        issue_segment<T>(An.src, An.L, ny2, nx2, stage, &ring.bars[s], lane);
-        ring.pending |= 1u << s;
-    }
-    // periodic x: the row's first node pulls from column nx-1 and its
-    // last node from column 0, which the staged halo does not hold
-    if (L.per_x && (tx == 0 || tx0 + TILE_W >= L.nx)) {
-#pragma unroll
-        for (int i = 0; i < 9; ++i) {
-            if (cxof(i) == 0) continue;
-            const int sy = wrap_or_clamp(y - cyof(i), L.ny, L.per_y);
-            const T *row = A.src + i * L.plane + (long long)sy * L.pitch;
-            if (cxof(i) == 1 && x0 == 0) d[i][0] = from_store<T>(L, i, Storage<T>::load1(row + (L.nx - 1)));
-            if (cxof(i) == -1) {
-                const int kl = L.nx - 1 - x0;
-#pragma unroll
-                for (int q = 0; q < VEC; ++q)
-                    if (q == kl) d[i][q] = from_store<T>(L, i, Storage<T>::load1(row));
-            }
-        }
-    }
-    // west / east edge nodes of a row that is not itself an edge row take
-    // the inner neighbour's (x + 1 or x - 1, same row) streamed values: from
-    // this thread's registers, from the left lane's, or (east edge opening
-    // its segment) from the slot filled from the halo above
-    if (col_edge && !row_edge) {
-        float left[9];
-#pragma unroll
-        for (int i = 0; i < 9; ++i) {
-            left[i] = __shfl_up_sync(0xffffffffu, d[i][VEC - 1], 1);
-            if (lane == 0) left[i] = d[i][1];
-        }
-#pragma unroll
-        for (int q = 0; q < VEC; ++q) {
-            const int x = x0 + q;
-            if (x != 0 && x != L.nx - 1) continue;
-            float dn[9], e[9];
-#pragma unroll
-            for (int i = 0; i < 9; ++i) {
-                if (x == 0) dn[i] = d[i][q < VEC - 1 ? q + 1 : q];            // q == 0 here: x0 == 0
-                else dn[i] = q > 0 ? d[i][q > 0 ? q - 1 : 0] : left[i];
-            }
-            extrapolate(L, x == 0 ? WEST : EAST, dn, e);
-#pragma unroll
-            for (int i = 0; i < 9; ++i) d[i][q] = e[i];
-        }
-    }
+    const bool wrap_end = L.per_x && (tx == 0 || tx0 + TILE_W >= L.nx);
     __syncwarp();   // candidate records visible to the whole warp
 
-    // ---- solid fraction (Eq. 14), owner and particle velocity per node:
-    // max over the tile's candidates, lowest particle id on ties
-    float phi[VEC], rxn[VEC], ryn[VEC];
-    int best[VEC], best_id[VEC];
+    // lane c < ncand: the segment's force / torque on candidate c so far
+    // (first pass, then second pass added)
+    float sgx = 0.f, sgy = 0.f, sgt = 0.f;
+    unsigned badmax = 0u;
+
+#pragma unroll 1
+    for (int pass = 0; pass < 2; ++pass) {
+        const int e = pass * (TILE_W / 2) + 2 * lane;    // the pair's first node within the segment
+        const int x = tx0 + e;
+
+        // ---- pull-stream from the staged rows: f_i(x, t+1) = f'_i(x - c_i, t)
+        float2 dk[9];
 #pragma unroll
-    for (int q = 0; q < VEC; ++q) { phi[q] = 0.f; rxn[q] = 0.f; ryn[q] = 0.f; best[q] = -1; best_id[q] = 0x7fffffff; }
-    // (ncand is warp-uniform; a segment no particle reaches skips all of it)
-    for (int c = 0; c < ncand; ++c) {
-        const float4 ra = crec[c], rb = crec[MAXC + c];
-        const float R = rb.x + ph.cut;
-        float dy = ((float)(y - ty0) - ra.z) - ra.w;
-        // short periodic axes: the stored image may lie several periods away
-        // (it is the one nearest the tile centre), so reduce by the nearest
-        // multiple of the period (exact: an integer multiple of an integer)
-        int ky = 0;                                     // PS: periods removed, for the table index
-        if constexpr (PS) {
+        for (int i = 0; i < 9; ++i) {
+            const T *row = stage + i * SW + H + e;
+            if (cxof(i) == 0) dk[i] = Storage<T>::lds2(row);
+            else dk[i] = make_float2(Storage<T>::lds1(row - cxof(i)), Storage<T>::lds1(row + 1 - cxof(i)));
+        }
+        // periodic x: the row's first node pulls from column nx-1 and its
+        // last node from column 0, which the staged halo does not hold
+        if (wrap_end) {
+#pragma unroll
+            for (int m = 0; m < 2; ++m) {
+                const int xm = x + m;
+                if (xm != 0 && xm != L.nx - 1) continue;
+#pragma unroll
+                for (int i = 0; i < 9; ++i) {
+                    if (cxof(i) == 0) continue;
+                    const T *src_row = plane_row<T>(A.src, L, i, y - cyof(i));
+                    if (cxof(i) == 1 && xm == 0) slot(dk[i], m) = Storage<T>::load1(src_row + (L.nx - 1));
+                    if (cxof(i) == -1 && xm == L.nx - 1) slot(dk[i], m) = Storage<T>::load1(src_row);
+                }
+            }
+        }
+        // west / east edge nodes of a row that is not itself an edge row take
+        // the inner neighbour's (same row) streamed values, from the stage
+        if (col_edge && !row_edge) {
+#pragma unroll
+            for (int m = 0; m < 2; ++m) {
+                const int xm = x + m;
+                if (xm != 0 && xm != L.nx - 1) continue;
+                float dn[9], ev[9];
+                staged_pull9<T>(L, stage, e + m + (xm == 0 ? 1 : -1), dn);
+                extrapolate(L, xm == 0 ? WEST : EAST, dn, ev);
+#pragma unroll
+                for (int i = 0; i < 9; ++i) slot(dk[i], m) = to_store<T>(L, i, ev[i]);
+            }
+        }
+        // the segment's last reads of the stage are done: recycle it for the
+        // segment STAGES items ahead
+        if (pass == 1) {
+            __syncwarp();
+            if (has_next) {
+                fence_proxy_async_smem();
+                issue_segment<T>(An.src, An.L, ny2, nx2, stage, &ring.bars[s], lane);
+                ring.pending |= 1u << s;
+            }
+        }
+        if (EDGES && row_edge) {
+            // south / north edge rows (corners included): neighbour on another row
+#pragma unroll
+            for (int m = 0; m < 2; ++m) {
+                if (x + m >= L.nx) continue;
+                const Pop9 ev = edge_values<T>(A.src, L, x + m, y);
+#pragma unroll
+                for (int i = 0; i < 9; ++i) slot(dk[i], m) = to_store<T>(L, i, ev.v[i]);
+            }
+        }
+
+        // ---- solid fraction (Eq. 14), owner and particle velocity per node:
+        // max over the tile's candidates, lowest particle id on ties
+        float phi[2] = {0.f, 0.f}, rxn[2] = {0.f, 0.f}, ryn[2] = {0.f, 0.f};
+        int best[2] = {-1, -1}, best_id[2] = {0x7fffffff, 0x7fffffff};
+        // (ncand is warp-uniform; a segment no particle reaches skips all of it)
+        for (int c = 0; c < ncand; ++c) {
+            const float4 ra = crec[c], rb = crec[MAXC + c];
+            const float R = rb.x + ph.cut;
+            float dy = ((float)(y - ty0) - ra.z) - ra.w;
+            // short periodic axes: the stored image may lie several periods away
+            // (it is the one nearest the tile centre), so reduce by the nearest
+            // multiple of the period (exact: an integer multiple of an integer)
+            int ky = 0;                                     // PS: periods removed, for the table index
             if (L.wrap_y) {
                 const float k = rintf(dy * __frcp_rn((float)L.ny));
                 dy = fmaf(-(float)L.ny, k, dy);
                 ky = (int)k;
             }
-        } else {
-            if (L.wrap_y) dy = fmaf(-(float)L.ny, rintf(dy * __frcp_rn((float)L.ny)), dy);
-        }
-        const float h2 = R * R - dy * dy;
-        if (h2 < 0.f) continue;                         // this row misses the disc tail
-        const float dx0 = ((float)(x0 - tx0) - ra.x) - ra.y;
-        if (!L.wrap_x) {
-            // the thread's 4 nodes span [dx0, dx0 + 3]
-            const float lo = dx0 > 0.f ? dx0 : (dx0 + (VEC - 1) < 0.f ? -(dx0 + (VEC - 1)) : 0.f);
-            if (lo * lo > h2) continue;
-        }
-        const int id = cid[c];
-        if constexpr (PS) {
-            // covered cell fraction (B = eps_s, Eq. 8): 1 once every corner is
-            // inside, else the particle's table entry for the cell.  The four
-            // nodes' entries are fetched before any is used, so their latencies
-            // overlap.  The centre's whole-cell offsets come packed in the record.
-            const int fpk = __float_as_int(crec[2 * MAXC + c].w);
-            const int K = ph.ck, S = 2 * K + 1;
-            const float *tab = A.B.cover + (long long)id * S * S;
-            const int iy = (y - ty0) - (int)(short)((unsigned)fpk >> 16) - L.ny * ky + K;
-            float pcq[VEC], dxq[VEC];
-#pragma unroll
-            for (int q = 0; q < VEC; ++q) {
-                float dx = dx0 + (float)q;
-                int kx = 0;
-                if (L.wrap_x) {
-                    const float k = rintf(dx * __frcp_rn((float)L.nx));
-                    dx = fmaf(-(float)L.nx, k, dx);
-                    kx = (int)k;
-                }
-                dxq[q] = dx;
-                const float d2 = dx * dx + dy * dy;
-                const float l = rb.x - sqrtf(d2);
-                const int ix = lane * VEC + q - (int)(short)(fpk & 0xffff) - L.nx * kx + K;
-                const bool inside = d2 <= R * R && l >= -ph.cut;
-                const bool look = inside && l < ph.cut && (unsigned)ix < (unsigned)S && (unsigned)iy < (unsigned)S;
-                pcq[q] = look ? __ldg(tab + iy * S + ix) : (inside && l >= ph.cut ? 1.0f : 0.f);
+            const float h2 = fmaf(-dy, dy, R * R);
+            if (h2 < 0.f) continue;                         // this row misses the disc tail
+            const float dx0 = ((float)e - ra.x) - ra.y;
+            if (!L.wrap_x) {
+                // the pair spans [dx0, dx0 + 1]
+                const float lo = dx0 > 0.f ? dx0 : (dx0 + 1.0f < 0.f ? -(dx0 + 1.0f) : 0.f);
+                if (lo * lo > h2) continue;
             }
+            const int id = cid[c];
+            if constexpr (PS) {
+                // covered cell fraction (B = eps_s, Eq. 8): 1 once every corner is
+                // inside, else the particle's table entry for the cell.  Both
+                // nodes' entries are fetched before either is used.  The
+                // centre's whole-cell offsets come packed in the record.
+                const int fpk = __float_as_int(crec[2 * MAXC + c].w);
+                const int K = ph.ck, S = 2 * K + 1;
+                const float *tab = A.B.cover + (long long)id * S * S;
+                const int iy = (y - ty0) - (int)(short)((unsigned)fpk >> 16) - L.ny * ky + K;
+                float pcq[2], dxq[2];
 #pragma unroll
-            for (int q = 0; q < VEC; ++q) {
-                const float pc = pcq[q];
-                if (!(pc > 0.f)) continue;
-                if (pc > phi[q] || (pc == phi[q] && id < best_id[q])) {
-                    phi[q] = pc; best[q] = c; best_id[q] = id; rxn[q] = dxq[q]; ryn[q] = dy;
+                for (int m = 0; m < 2; ++m) {
+                    float dx = dx0 + (float)m;
+                    int kx = 0;
+                    if (L.wrap_x) {
+                        const float k = rintf(dx * __frcp_rn((float)L.nx));
+                        dx = fmaf(-(float)L.nx, k, dx);
+                        kx = (int)k;
+                    }
+                    dxq[m] = dx;
+                    const float d2 = fmaf(dx, dx, dy * dy);
+                    const float l = rb.x - sqrtf(d2);
+                    const int ix = e + m - (int)(short)(fpk & 0xffff) - L.nx * kx + K;
+                    const bool inside = d2 <= R * R && l >= -ph.cut;
+                    const bool look = inside && l < ph.cut && (unsigned)ix < (unsigned)S && (unsigned)iy < (unsigned)S;
+                    pcq[m] = look ? __ldg(tab + iy * S + ix) : (inside && l >= ph.cut ? 1.0f : 0.f);
                 }
-            }
-        } else {
 #pragma unroll
-            for (int q = 0; q < VEC; ++q) {
-                float dx = dx0 + (float)q;
-                if (L.wrap_x) dx = fmaf(-(float)L.nx, rintf(dx * __frcp_rn((float)L.nx)), dx);
-                const float d2 = dx * dx + dy * dy;
-                if (d2 > R * R) continue;
-                const float l = rb.x - sqrtf(d2);
-                if (l < -ph.cut) continue;
-                // (1 + tanh(2l/eps)) / 2 == 1 / (1 + exp(-4l/eps))
-                const float pc = __frcp_rn(1.0f + expf(-ph.four_over_eps * l));
-                if (pc > phi[q] || (pc == phi[q] && pc > 0.f && id < best_id[q])) {
-                    phi[q] = pc; best[q] = c; best_id[q] = id; rxn[q] = dx; ryn[q] = dy;
+                for (int m = 0; m < 2; ++m) {
+                    const float pc = pcq[m];
+                    if (!(pc > 0.f)) continue;
+                    if (pc > phi[m] || (pc == phi[m] && id < best_id[m])) {
+                        phi[m] = pc; best[m] = c; best_id[m] = id; rxn[m] = dxq[m]; ryn[m] = dy;
+                    }
+                }
+            } else {
+#pragma unroll
+                for (int m = 0; m < 2; ++m) {
+                    float dx = dx0 + (float)m;
+                    if (L.wrap_x) dx = fmaf(-(float)L.nx, rintf(dx * __frcp_rn((float)L.nx)), dx);
+                    const float d2 = fmaf(dx, dx, dy * dy);
+                    if (d2 > R * R) continue;
+                    const float l = rb.x - sqrtf(d2);
+                    if (l < -ph.cut) continue;
+                    // (1 + tanh(2l/eps)) / 2 == 1 / (1 + exp(-4l/eps))
+                    const float pc = __frcp_rn(1.0f + expf(-ph.four_over_eps * l));
+                    if (pc > phi[m] || (pc == phi[m] && pc > 0.f && id < best_id[m])) {
+                        phi[m] = pc; best[m] = c; best_id[m] = id; rxn[m] = dx; ryn[m] = dy;
+                    }
                 }
             }
         }
-    }
 
-    // warps with no node inside any particle's phi tail collide without the force term
-    const bool coupled = ncand > 0 && __any_sync(0xffffffffu, max(max(best[0], best[1]), max(best[2], best[3])) >= 0);
-    float acc[VEC][3];
-    unsigned badmax = 0u;
+        // warps with no node inside any particle's phi tail collide without the force term
+        const bool coupled = ncand > 0 && __any_sync(0xffffffffu, max(best[0], best[1]) >= 0);
+        const bool act_a = x < L.nx, act_b = x + 1 < L.nx;
 
-    // nodes in pairs (2h, 2h + 1) on the paired FP32 instructions
-#pragma unroll
-    for (int h = 0; h < VEC / 2; ++h) {
-        const int qa = 2 * h, qb = 2 * h + 1;
-        float2 dk[9];
-#pragma unroll
-        for (int i = 0; i < 9; ++i) dk[i] = make_float2(d[i][qa], d[i][qb]);
-        if (EDGES && row_edge) {
-            // south / north edge rows (corners included): neighbour on another row
-            if (x0 + qa < L.nx) {
-                const Pop9 e = edge_values<T>(A.src, L, x0 + qa, y);
-#pragma unroll
-                for (int i = 0; i < 9; ++i) dk[i].x = e.v[i];
-            }
-            if (x0 + qb < L.nx) {
-                const Pop9 e = edge_values<T>(A.src, L, x0 + qb, y);
-#pragma unroll
-                for (int i = 0; i < 9; ++i) dk[i].y = e.v[i];
-            }
+        // ---- moments (Eq. 5, Eq. 16): of the stored values, then physical
+        const float2 ms = add2(add2(add2(add2(dk[0], dk[1]), add2(dk[2], dk[3])),
+                                    add2(add2(dk[4], dk[5]), add2(dk[6], dk[7]))), dk[8]);
+        const float2 jxs = add2(add2(sub2(dk[1], dk[3]), sub2(dk[5], dk[6])), sub2(dk[8], dk[7]));
+        const float2 jys = sub2(add2(sub2(dk[2], dk[4]), add2(dk[5], dk[6])), add2(dk[7], dk[8]));
+        float2 drho = ms, jx = jxs, jy = jys;
+        if constexpr (!std::is_same<T, float>::value) {
+            const float2 q = f2(L.ref_q);
+            drho = fma2(q, ms, f2(L.ref_m[0]));
+            jx = fma2(q, jxs, f2(L.ref_m[1]));
+            jy = fma2(q, jys, f2(L.ref_m[2]));
         }
-
-        // ---- moments (Eq. 5, Eq. 16)
-        const float2 drho = add2(add2(add2(add2(dk[0], dk[1]), add2(dk[2], dk[3])),
-                                      add2(add2(dk[4], dk[5]), add2(dk[6], dk[7]))), dk[8]);
         const float2 rho = add2(f2(1.0f), drho);
-        const float2 jx = add2(add2(sub2(dk[1], dk[3]), sub2(dk[5], dk[6])), sub2(dk[8], dk[7]));
-        const float2 jy = sub2(add2(sub2(dk[2], dk[4]), add2(dk[5], dk[6])), add2(dk[7], dk[8]));
         // u* (Eq. 16); CUDA's correctly rounded reciprocal (a biased one would
         // bias u* the same way on every node and step)
         const float2 inv = make_float2(__frcp_rn(rho.x), __frcp_rn(rho.y));
         const float2 ua = mul2(jx, inv), va = mul2(jy, inv);
-        const bool act_a = x0 + qa < L.nx, act_b = x0 + qb < L.nx;
         if (MODE == MODE_STEP) {
             // unstable: rho <= 0 or not finite (a non-finite population makes
             // rho non-finite); as unsigned, bits(rho) - 1 exceeds the largest
@@ -904,12 +930,10 @@ __device__ __forceinline__ bool sweep_segment(const SweepArgs<T> &A, int y, int 
             badmax = max(badmax, act_a ? __float_as_uint(rho.x) - 1u : 0u);
             badmax = max(badmax, act_b ? __float_as_uint(rho.y) - 1u : 0u);
         }
-        acc[qa][0] = acc[qa][1] = acc[qa][2] = 0.f;
-        acc[qb][0] = acc[qb][1] = acc[qb][2] = 0.f;
 
         if (!coupled) {
             if (MODE == MODE_FIELDS) {
-                const long long o = (long long)y * L.nx + x0 + qa;
+                const long long o = (long long)y * L.nx + x;
                 if (act_a) {
                     if (A.fo.rho) A.fo.rho[o] = rho.x;
                     if (A.fo.ux) A.fo.ux[o] = ua.x;
@@ -924,7 +948,7 @@ __device__ __forceinline__ bool sweep_segment(const SweepArgs<T> &A, int y, int 
                 }
                 continue;
             }
-            collide_plain2(dk, ph.omega, drho, jx, jy, ua, va);
+            collide_plain2<T>(dk, L, ph.omega, ms, jxs, jys, jx, jy, ua, va);
         } else {
             // u_s - u* from the particle velocity carried as FP32 hi + lo:
             // u_s = U + omega x r with r the node's offset from the centre
@@ -932,24 +956,23 @@ __device__ __forceinline__ bool sweep_segment(const SweepArgs<T> &A, int y, int 
             const float uas[2] = {ua.x, ua.y}, vas[2] = {va.x, va.y};
 #pragma unroll
             for (int m = 0; m < 2; ++m) {
-                const int q = qa + m;
-                const int b = best[q];
+                const int b = best[m];
                 if (b >= 0) {
                     const float4 rb = crec[MAXC + b], rl = crec[2 * MAXC + b];
-                    du[m] = fmaf(-rb.w, ryn[q], rb.y - uas[m]) + fmaf(-rl.z, ryn[q], rl.x);
-                    dv[m] = fmaf(rb.w, rxn[q], rb.z - vas[m]) + fmaf(rl.z, rxn[q], rl.y);
+                    du[m] = fmaf(-rb.w, ryn[m], rb.y - uas[m]) + fmaf(-rl.z, ryn[m], rl.x);
+                    dv[m] = fmaf(rb.w, rxn[m], rb.z - vas[m]) + fmaf(rl.z, rxn[m], rl.y);
                 }
             }
             const float2 dux = make_float2(du[0], du[1]), duy = make_float2(dv[0], dv[1]);
             const float2 usx = add2(ua, dux), usy = add2(va, duy);
-            const float2 phq = make_float2(phi[qa], phi[qb]);
+            const float2 phq = make_float2(phi[0], phi[1]);
             // ---- corrected velocity (Eq. 17)
             // (PS-LBM: f^eq takes the fluid velocity u*, there is no correction)
             const float2 hph = mul2(f2(PS ? 0.0f : 0.5f), phq);
             const float2 ux = fma2(hph, dux, ua), uy = fma2(hph, duy, va);
 
             if (MODE == MODE_FIELDS) {
-                const long long o = (long long)y * L.nx + x0 + qa;
+                const long long o = (long long)y * L.nx + x;
                 if (act_a) {
                     if (A.fo.rho) A.fo.rho[o] = rho.x;
                     if (A.fo.ux) A.fo.ux[o] = ux.x;
@@ -965,88 +988,47 @@ __device__ __forceinline__ bool sweep_segment(const SweepArgs<T> &A, int y, int 
                 continue;
             }
             const float2 prho = mul2(rho, phq);
-            collide2(dk, ph.omega, drho, rho, jx, jy, ux, uy, mul2(f2(ph.kf), prho), prho, dux, duy, usx, usy, ua,
-                     va);
+            collide2<T>(dk, L, ph.omega, ms, jxs, jys, rho, ux, uy, mul2(f2(ph.kf), prho), prho, dux, duy, usx, usy,
+                        ua, va);
 
-            // ---- Eqs. 18-19 per node, by the closed form sum_i F_i c_i = kf rho (u_s - u*)
+            // ---- Eqs. 18-19 per node, by the closed form sum_i F_i c_i = kf rho (u_s - u*),
+            // summed per candidate over the pass (the lane's two nodes, then a
+            // fixed shuffle tree) and added to that candidate's lane
+            const int own_a = act_a ? best[0] : -1, own_b = act_b ? best[1] : -1;
+            const float sa = -prho.x * ph.kforce, sb = -prho.y * ph.kforce;
+            const float gax = sa * du[0], gay = sa * dv[0], gbx = sb * du[1], gby = sb * dv[1];
+            const float ta = fmaf(rxn[0], gay, -(ryn[0] * gax)), tb = fmaf(rxn[1], gby, -(ryn[1] * gbx));
+            for (int c = 0; c < ncand; ++c) {
+                float v0 = 0.f, v1 = 0.f, v2 = 0.f;
+                if (own_a == c) { v0 = gax; v1 = gay; v2 = ta; }
+                if (own_b == c) { v0 += gbx; v1 += gby; v2 += tb; }
+                if (!__any_sync(0xffffffffu, own_a == c || own_b == c)) continue;
 #pragma unroll
-            for (int m = 0; m < 2; ++m) {
-                const int q = qa + m;
-                if (x0 + q < L.nx && best[q] >= 0) {
-                    const float sg = -(m ? prho.y : prho.x) * ph.kforce;
-                    const float gx = sg * du[m], gy = sg * dv[m];
-                    acc[q][0] = gx; acc[q][1] = gy; acc[q][2] = rxn[q] * gy - ryn[q] * gx;
+                for (int o = 16; o > 0; o >>= 1) {
+                    v0 += __shfl_xor_sync(0xffffffffu, v0, o);
+                    v1 += __shfl_xor_sync(0xffffffffu, v1, o);
+                    v2 += __shfl_xor_sync(0xffffffffu, v2, o);
                 }
+                if (lane == c) { sgx += v0; sgy += v1; sgt += v2; }
             }
         }
+
+        // ---- store the collided pair: one contiguous run per plane and pass
+        T *base = A.dst + (long long)y * L.pitch + x;
+        if (act_b) {
 #pragma unroll
-        for (int i = 0; i < 9; ++i) {
-            d[i][qa] = dk[i].x;
-            d[i][qb] = dk[i].y;
+            for (int i = 0; i < 9; ++i) Storage<T>::store2(base + i * L.plane, dk[i]);
+        } else if (act_a) {
+#pragma unroll
+            for (int i = 0; i < 9; ++i) Storage<T>::store1(base + i * L.plane, dk[i].x);
         }
     }
 
     if (MODE == MODE_FIELDS) return true;
     if (__any_sync(0xffffffffu, badmax > 0x7f7ffffeu) && lane == 0) atomicOr(A.err, ERR_UNSTABLE);
-
-    // ---- store the collided populations.  Without edge code one branch for
-    // the whole segment; with it the per-direction form, which measured
-    // faster in that larger kernel (its code layout is sensitive)
-    if (!EDGES) {
-        T *base = A.dst + (long long)y * L.pitch + x0;
-        if (x0 + VEC <= L.nx) {
-#pragma unroll
-            for (int i = 0; i < 9; ++i)
-                Storage<T>::store4(base + i * L.plane, to_store4<T>(L, i, make_float4(d[i][0], d[i][1], d[i][2], d[i][3])));
-        } else {
-#pragma unroll
-            for (int i = 0; i < 9; ++i) {
-                const float4 v = to_store4<T>(L, i, make_float4(d[i][0], d[i][1], d[i][2], d[i][3]));
-                const float vv[VEC] = {v.x, v.y, v.z, v.w};
-#pragma unroll
-                for (int q = 0; q < VEC; ++q)
-                    if (x0 + q < L.nx) Storage<T>::store1(base + i * L.plane + q, vv[q]);
-            }
-        }
-    } else {
-        const bool full = x0 + VEC <= L.nx;
-#pragma unroll
-        for (int i = 0; i < 9; ++i) {
-            T *row = A.dst + i * L.plane + (long long)y * L.pitch;
-            const float4 v = to_store4<T>(L, i, make_float4(d[i][0], d[i][1], d[i][2], d[i][3]));
-            if (full) {
-                Storage<T>::store4(row + x0, v);
-            } else {
-                const float vv[VEC] = {v.x, v.y, v.z, v.w};
-#pragma unroll
-                for (int q = 0; q < VEC; ++q)
-                    if (x0 + q < L.nx) Storage<T>::store1(row + x0 + q, vv[q]);
-            }
-        }
-    }
-
-    // ---- this row segment's force / torque per candidate (fixed shuffle tree)
-    for (int c = 0; c < ncand; ++c) {
-        if (!coupled) {
-            if (lane == 0)
-                A.partial[((long long)tile * MAXC + c) * TILE_H + (y - ty0)] = make_float4(0.f, 0.f, 0.f, 0.f);
-            continue;
-        }
-        float v0 = 0.f, v1 = 0.f, v2 = 0.f;
-#pragma unroll
-        for (int q = 0; q < VEC; ++q)
-            if (best[q] == c) { v0 += acc[q][0]; v1 += acc[q][1]; v2 += acc[q][2]; }
-        if (__any_sync(0xffffffffu, v0 != 0.f || v1 != 0.f || v2 != 0.f)) {
-#pragma unroll
-            for (int o = 16; o > 0; o >>= 1) {
-                v0 += __shfl_xor_sync(0xffffffffu, v0, o);
-                v1 += __shfl_xor_sync(0xffffffffu, v1, o);
-                v2 += __shfl_xor_sync(0xffffffffu, v2, o);
-            }
-        }
-        if (lane == 0)
-            A.partial[((long long)tile * MAXC + c) * TILE_H + (y - ty0)] = make_float4(v0, v1, v2, 0.f);
-    }
+    // ---- this row segment's force / torque per candidate (zero where no node is owned)
+    if (lane < ncand)
+        A.partial[((long long)tile * MAXC + lane) * TILE_H + (y - ty0)] = make_float4(sgx, sgy, sgt, 0.f);
     return true;
 }
 
@@ -1069,12 +1051,17 @@ struct SweepSmem {
     }
 };
 
+// Resident warps per SM the sweep kernels are compiled for: W warps per
+// block and SWEEP_SM_WARPS / W blocks per SM (registers capped at 96 per
+// thread for W = 2 and 4; W = 8 holds two blocks, 16 warps).
+constexpr int SWEEP_SM_WARPS = 20;
+
 // The sweep over one lattice.  Persistent: warps take row segments
 // round-robin (neighbouring warps on neighbouring segments); each warp keeps
 // STAGES segments staged ahead.  W warps per block (rows in flight per
-// block); every W caps registers at 128 per thread.
+// block).
 template <typename T, int MODE, bool EDGES, int W = SWEEP_WARPS, bool PS = false>
-__global__ void __launch_bounds__(W * 32, 16 / W)
+__global__ void __launch_bounds__(W * 32, SWEEP_SM_WARPS / W)
 sweep_kernel(const __grid_constant__ SweepArgs<T> one)
 {
     constexpr int SW = segw_of<T>();
@@ -1149,10 +1136,13 @@ struct Cursor {
     int item, lat, y, tx;
 };
 
+// Move cursor c (at an earlier item, or c.lat = 0) forward to `item`: a
+// warp's items only grow, so its lattice is found by stepping on from the
+// last one (a few lattices at most per step of the work list).
 template <typename T>
 __device__ __forceinline__ void cursor_seek(const BatchArgs<T> &ba, Cursor &c, int item) {
     c.item = item;
-    c.lat = batch_find(ba.item_start, ba.n, item);
+    while (c.lat + 1 < ba.n && ba.item_start[c.lat + 1] <= item) ++c.lat;
     const int local = item - ba.item_start[c.lat];
     const int ntx = ba.a[c.lat].L.ntx;
     c.y = local / ntx;
@@ -1165,7 +1155,7 @@ __device__ __forceinline__ void cursor_seek(const BatchArgs<T> &ba, Cursor &c, i
 // (DRAM page locality); each item finds its lattice by a binary search in the
 // parameter space.
 template <typename T, int MODE, int W = SWEEP_WARPS>
-__global__ void __launch_bounds__(W * 32, 16 / W)
+__global__ void __launch_bounds__(W * 32, SWEEP_SM_WARPS / W)
 sweep_batch_kernel(const __grid_constant__ BatchArgs<T> ba)
 {
     constexpr int SW = segw_of<T>();
@@ -1189,7 +1179,7 @@ sweep_batch_kernel(const __grid_constant__ BatchArgs<T> ba)
 
     const int nitems = ba.item_start[ba.n];
     const int gw = blockIdx.x * W + warp, nw = gridDim.x * W;
-    Cursor cur, ahead;
+    Cursor cur{0, 0, 0, 0}, ahead{0, 0, 0, 0};
     ring.parity = 0;
     ring.pending = 0;
     for (int s = 0; s < STAGES; ++s) {
@@ -1270,6 +1260,14 @@ struct PartArgs {
     int *err;
     int track = -1;             // moving frame: tracked particle, -1 (the default) when off
     double track_x = 0.0;       // its reference x
+    // A strip of the lattice (L is the whole lattice): bins hold the tile rows
+    // [ty_lo, ty_hi) only, local tile index (ty - ty_lo) * ntx + tx.
+    int ty_lo = 0, ty_hi = 1 << 30;
+    // phase 0: the whole update; 1: only the force / torque and repulsion
+    // sums of this strip's bins, written to fpart (5 per particle: Fx, Fy, T,
+    // repulsion x, y); 2: the rest of the update from the sums in fpart.
+    int phase = 0;
+    double *fpart = nullptr;
 };
 
 // Moving computational domain (Sec. 3.5): the frame's move at the end of a
@@ -1337,7 +1335,7 @@ __device__ __forceinline__ void particle_forces(const PartArgs &A, int p, int la
         const int k = e / TILE_H, row = e - k * TILE_H;
         const int ts = bin_in.pslot[(long long)p * MAXT + k];
         if (ts < 0) continue;
-        const int ty = (ts / MAXC) / L.ntx;
+        const int ty = (ts / MAXC) / L.ntx + A.ty_lo;
         if (ty * TILE_H + row >= L.ny) continue;
         const float4 v = partial[(long long)ts * TILE_H + row];
         fx += (double)v.x; fy += (double)v.y; tq += (double)v.z;
@@ -1377,7 +1375,7 @@ __device__ __forceinline__ void particle_forces(const PartArgs &A, int p, int la
             int mxi = (int)floor(mx), myi = (int)floor(my);
             mxi = mxi < 0 ? 0 : (mxi > L.nx - 1 ? L.nx - 1 : mxi);
             myi = myi < 0 ? 0 : (myi > L.ny - 1 ? L.ny - 1 : myi);
-            if ((myi / TILE_H) * L.ntx + mxi / TILE_W == t) contact |= 1u << sl;
+            if ((myi / TILE_H) * L.ntx + mxi / TILE_W == t + A.ty_lo * L.ntx) contact |= 1u << sl;
         }
         while (contact) {                         // increasing partner id
             int sel = -1, jmin = 0x7fffffff;
@@ -1514,9 +1512,13 @@ __device__ __forceinline__ void particle_bin(const PartArgs &A, int p, int lane,
     }
     for (int k = lane; k < total; k += 32) {
         const int ty = range_at(ay, k / NX), tx = range_at(ax, k - (k / NX) * NX);
-        const int t = ty * L.ntx + tx;
-        const int s = atomicAdd(&bin_out.count[t], 1);
         int entry = -1;
+        if (ty < A.ty_lo || ty >= A.ty_hi) {       // another strip's tile
+            bin_out.pslot[(long long)p * MAXT + k] = entry;
+            continue;
+        }
+        const int t = (ty - A.ty_lo) * L.ntx + tx;
+        const int s = atomicAdd(&bin_out.count[t], 1);
         if (s < MAXC) {
             double cx = nX - (double)(tx * TILE_W), cy = nY - (double)(ty * TILE_H);
             if (L.per_x) {
@@ -1570,7 +1572,19 @@ particles_kernel(const __grid_constant__ PartArgs one, const PartArgs *__restric
     };
     int p = 0;
     const PartArgs *A = locate(blockIdx.x * PART_WARPS + w, p);
-    if (A && A->integrate) particle_forces(*A, p, lane, sh[w]);
+    const int phase = BATCH ? 0 : one.phase;       // (uniform over the launch)
+    if (A && A->integrate && phase != 2) particle_forces(*A, p, lane, sh[w]);
+    if (phase == 1) {
+        if (A && A->integrate && lane == 0) {
+            double *o = A->fpart + 5 * (long long)p;
+            o[0] = sh[w].fx; o[1] = sh[w].fy; o[2] = sh[w].tq; o[3] = sh[w].cx; o[4] = sh[w].cy;
+        }
+        return;
+    }
+    if (phase == 2 && A && lane == 0) {
+        const double *o = A->fpart + 5 * (long long)p;
+        sh[w].fx = o[0]; sh[w].fy = o[1]; sh[w].tq = o[2]; sh[w].cx = o[3]; sh[w].cy = o[4];
+    }
     __syncthreads();
     if (w == 0 && lane < PART_WARPS) {
         int q = 0;
@@ -1734,8 +1748,8 @@ __global__ void init_kernel(T *__restrict__ dst, Lattice L, float drho, float ux
 #pragma unroll
         for (int j = 1; j < 9; ++j)
             if (i == j) v = e[j];
-        Storage<T>::store1(dst + i * L.plane + (long long)y * L.pitch + x,
-                           std::is_same<T, float>::value ? v : (v - ref_e_of(L, i)) * L.ref_iq);
+        // (16-bit storage: the initial state is the reference state itself, s_i = 0)
+        Storage<T>::store1(dst + i * L.plane + (long long)y * L.pitch + x, std::is_same<T, float>::value ? v : 0.0f);
     }
 }
 
