@@ -55,7 +55,9 @@ typedef enum {
 typedef enum {
     DILBM_FP32 = 0,            /* populations stored as FP32 deviations f_i - w_i */
     DILBM_FP16_DEV = 1,        /* stored as FP16 deviations, FP32 arithmetic */
-    DILBM_BF16_DEV = 2         /* stored as BF16 deviations, FP32 arithmetic */
+    DILBM_BF16_DEV = 2         /* stored as BF16 deviations, FP32 arithmetic.  Regression
+                                  only, not a reduced-precision path held to the drag bound:
+                                  its 8-bit mantissa misses a 1e-3 drag error on the cylinder */
 } dilbm_storage;
 
 typedef enum {
@@ -142,6 +144,51 @@ int dilbm_create(const dilbm_grid *grid, dilbm_lattice lattice, double tau,
  * caller is capturing that stream, where the launches are issued directly).
  */
 int dilbm_step(dilbm_ctx *ctx, long long nsteps);
+
+/*
+ * One lattice split over ranks in horizontal strips (one process per GPU).
+ * Each rank holds rows [y0, y1) of the lattice and a copy of every particle;
+ * a step is the procedure of Sec. 2.3 on those rows, with two exchanges
+ * between ranks that the caller carries out (with NCCL, MPI or host copies):
+ *   - pull streaming (Eq. 13, left side) across a cut needs the neighbour's
+ *     post-collision row beside it: the three populations crossing each cut,
+ *     sent as whole rows of the nine planes;
+ *   - the force and torque of Eqs. 18-19 (and the Wan-Turek repulsion of
+ *     Eq. 28) are sums over nodes, so each rank adds up the nodes it holds and
+ *     the per-particle sums are added over ranks before the rigid-body update
+ *     (Eqs. 22-24), which every rank then applies to its copy alike.
+ *
+ * dilbm_create_strip: as dilbm_create, for rows [y0, y1) of the lattice `grid`
+ *   describes: y0 and y1 multiples of 8 (y1 may be ny), at least two rows,
+ *   not the whole lattice.  Cuts of a non-periodic y axis at 0 and ny are the
+ *   lattice's own sides; every other side (and both on a periodic y axis) is a
+ *   cut.  Errors as dilbm_create, and INVALID_ARG for a bad range or a periodic
+ *   y axis shorter than the discs' reach plus 8 rows.  dilbm_step,
+ *   dilbm_set_moving_frame and batches refuse a strip.
+ * dilbm_strip_begin: queue this step's sweep of the strip (its halos are the
+ *   rows received in the previous exchange; the initial state at the start),
+ *   the per-particle sums over the strip's nodes, and copies of the strip's
+ *   first and last rows into the send buffers.  Asynchronous.
+ * Exchange (caller, after the stream has reached that point): recv_south <-
+ *   the south neighbour's send_north, recv_north <- the north neighbour's
+ *   send_south (row_elems stored elements each, the storage type's), and
+ *   fpart (np x 5 doubles: Fx, Fy, T, repulsion x, y) <- its sum over all
+ *   ranks, identical on every rank.
+ * dilbm_strip_end: queue the rigid-body update with the summed fpart and the
+ *   binning for the next step.  Asynchronous.
+ * dilbm_strip_buffers: device addresses of the exchange buffers (owned by the
+ *   context, valid until dilbm_destroy); any pointer may be NULL.
+ * Every other call (dilbm_forces, dilbm_fields on the strip's rows,
+ * dilbm_get/set_populations of the strip's rows, dilbm_sync) works as on a
+ * whole lattice.
+ */
+int dilbm_create_strip(const dilbm_grid *grid, dilbm_lattice lattice, double tau, double interface_width,
+                       const dilbm_particle *particles, int np, int y0, int y1, void *cuda_stream,
+                       dilbm_ctx **out);
+int dilbm_strip_begin(dilbm_ctx *ctx);
+int dilbm_strip_end(dilbm_ctx *ctx);
+int dilbm_strip_buffers(dilbm_ctx *ctx, double **fpart, void **send_south, void **send_north, void **recv_south,
+                        void **recv_north, long long *row_elems);
 
 /*
  * Hydrodynamic force and torque of the last step (Eqs. 18-19, lattice units,
@@ -347,6 +394,14 @@ typedef enum {
 /* dilbm_server_config.storage: each job keeps its own grid.storage; the
  * server steps one batch per storage type, all by the same macro-steps. */
 #define DILBM_STORAGE_PER_JOB (-1)
+/* dilbm_server_config.storage: FP16 deviation storage for the jobs whose flow
+ * 11 stored mantissa bits resolve, FP32 for the others.  A job runs in FP32
+ * when its tau exceeds auto_tau_max or its discs cover more than
+ * auto_area_max of the lattice: a slow, viscous flow (large tau) or a packed
+ * bed of discs needs a pressure gradient whose density deviation is large
+ * beside the velocity signal the force of Eqs. 18-19 depends on, and FP16
+ * stores the two together.  The server steps one batch per storage type. */
+#define DILBM_STORAGE_AUTO (-2)
 
 typedef struct {
     int storage;                /* dilbm_storage of every job (a job's grid.storage is ignored),
@@ -355,6 +410,8 @@ typedef struct {
     long long macro_steps;      /* most steps per macro-step, >= 1 */
     double memory_budget;       /* bytes the resident jobs may take; <= 0: 90% of free device memory at create */
     int policy;                 /* dilbm_admit_policy */
+    double auto_tau_max;        /* DILBM_STORAGE_AUTO: largest tau run in FP16 (<= 0: 0.6) */
+    double auto_area_max;       /* DILBM_STORAGE_AUTO: largest disc area fraction run in FP16 (<= 0: 0.05) */
 } dilbm_server_config;
 
 typedef struct {
@@ -382,6 +439,7 @@ typedef struct {
     long long steps_done;
     double arrival, admitted, finished;   /* server clock; -1 until reached */
     unsigned long long footprint;         /* dilbm_footprint of the job */
+    int storage;                          /* the dilbm_storage the job runs in */
 } dilbm_job_status;
 
 typedef struct {

@@ -72,7 +72,17 @@ struct dilbm_ctx {
     double track_x = 0.0;             // its reference x
     long long *frame_off = nullptr;   // device: columns the frame has moved, allocated on first use
     float *cover = nullptr;           // PS: per-particle covered-area tables (grown by upload_particles)
-    void *owned[32] = {};
+    // A strip of a lattice decomposed over ranks (dilbm_create_strip): L holds
+    // rows [y0, y0 + L.ny) with halo rows across its cuts, Lg the whole
+    // lattice (the particles' geometry), tile rows [ty_lo, ty_lo + L.nty).
+    bool strip = false;
+    int y0 = 0, ty_lo = 0;
+    Lattice Lg{};
+    void *xsend[2] = {nullptr, nullptr};   // this strip's first / last row (9 plane rows), for the neighbours
+    void *xrecv[2] = {nullptr, nullptr};   // the rows just south / north of it (the sweep's halos)
+    double *fpart = nullptr;               // per particle: this strip's Fx, Fy, T, repulsion x, y
+    bool strip_open = false;               // between dilbm_strip_begin and dilbm_strip_end
+    void *owned[40] = {};
     int nowned = 0;
 };
 
@@ -152,10 +162,16 @@ int check_reach(double cut_d, const dilbm_particle *p, int np) {
     return DILBM_OK;
 }
 
-PartArgs particle_args(const dilbm_ctx *c, int cur, int integrate) {
+PartArgs particle_args(const dilbm_ctx *c, int cur, int integrate, int phase = 0) {
     const int nxt = integrate ? cur ^ 1 : cur;
     PartArgs a{};
-    a.L = c->L;
+    a.L = c->strip ? c->Lg : c->L;
+    if (c->strip) {
+        a.ty_lo = c->ty_lo;
+        a.ty_hi = c->ty_lo + c->L.nty;
+        a.phase = phase;
+        a.fpart = c->fpart;
+    }
     a.ph = c->ph;
     a.P = c->P;
     a.bp = c->bp;
@@ -174,13 +190,13 @@ PartArgs particle_args(const dilbm_ctx *c, int cur, int integrate) {
     return a;
 }
 
-int launch_particles(dilbm_ctx *c, int integrate) {
+int launch_particles(dilbm_ctx *c, int integrate, int phase = 0) {
     const int np = c->np;
-    particles_kernel<false><<<(np + PART_WARPS - 1) / PART_WARPS, PART_WARPS * 32, 0, c->stream>>>(particle_args(c, c->cur, integrate),
-                                                                          nullptr, BatchIndex{});
+    particles_kernel<false><<<(np + PART_WARPS - 1) / PART_WARPS, PART_WARPS * 32, 0, c->stream>>>(
+        particle_args(c, c->cur, integrate, phase), nullptr, BatchIndex{});
     DILBM_CUDA(cudaGetLastError());
     c->launches += 1;
-    if (c->method == DILBM_METHOD_PS) {
+    if (c->method == DILBM_METHOD_PS && phase != 1) {
         // the covered-area tables of the positions just written
         const int pout = integrate ? c->cur ^ 1 : c->cur;
         cover_kernel<<<np, dim3(COVER_BX, COVER_BY), 0, c->stream>>>(c->cover, c->P.x[pout], c->P.y[pout], c->P.r, np,
@@ -545,11 +561,11 @@ extern "C" {
 
 const char *dilbm_last_error(void) { return g_err.c_str(); }
 
-int dilbm_create(const dilbm_grid *g, dilbm_lattice lattice, double tau, double interface_width,
-                 const dilbm_particle *particles, int np, void *cuda_stream, dilbm_ctx **out) {
-    const dilbm::TraceRange trace("dilbm_create");
-    if (!g || !out) return fail(DILBM_ERR_INVALID_ARG, "grid and out must not be NULL");
-    *out = nullptr;
+}  // extern "C"
+
+// A context for rows [y0, y1) of the lattice (the whole lattice: 0, ny).
+static int create_ctx(const dilbm_grid *g, dilbm_lattice lattice, double tau, double interface_width,
+                      const dilbm_particle *particles, int np, void *cuda_stream, int y0, int y1, dilbm_ctx **out) {
     int rc = dilbm::check_problem(g, lattice, tau, interface_width, particles, np);
     if (rc) return rc;
 
@@ -586,10 +602,29 @@ int dilbm_create(const dilbm_grid *g, dilbm_lattice lattice, double tau, double 
             const double cu = cxof(i) * ux + cyof(i) * uy;
             const double e = w[i] * r0 * (1.0 + 3.0 * cu + 4.5 * cu * cu - 1.5 * (ux * ux + uy * uy)) - w[i];
             L.ref_e[i] = wide ? 0.0f : (float)e;
-            L.ref_ne[i] = wide ? 0.0f : (float)(-(double)L.ref_e[i] / q);
         }
         L.ref_q = (float)q;
         L.ref_iq = (float)(1.0 / q);
+        // the reference's moments in the collision's moment form (Eq. 2):
+        // m0 = rho - 1, B = rho u0, M = rho u0 u0^T
+        const double m[6] = {r0 - 1.0, r0 * ux, r0 * uy, r0 * ux * ux, r0 * uy * uy, r0 * ux * uy};
+        for (int k = 0; k < 6; ++k) L.ref_m[k] = wide ? 0.0f : (float)m[k];
+    }
+    const bool strip = y0 > 0 || y1 < g->ny;
+    if (strip) {
+        // the particles keep the whole lattice's geometry; the sweep sees
+        // rows [y0, y1) with halo rows beyond each cut
+        c->strip = true;
+        c->Lg = L;
+        c->y0 = y0;
+        c->ty_lo = y0 / TILE_H;
+        const bool cut_s = y0 > 0 || L.per_y, cut_n = y1 < g->ny || L.per_y;
+        L.ny = y1 - y0;
+        L.plane = (long long)L.pitch * L.ny;
+        L.nty = (L.ny + TILE_H - 1) / TILE_H;
+        L.per_y = 0;
+        if (cut_s) L.side_kind[SOUTH] = SIDE_HALO;
+        if (cut_n) L.side_kind[NORTH] = SIDE_HALO;
     }
     c->ntiles = L.ntx * L.nty;
     Physics &ph = c->ph;
@@ -655,6 +690,22 @@ int dilbm_create(const dilbm_grid *g, dilbm_lattice lattice, double tau, double 
     c->P.r = pd + 4 * npa; c->P.ux = pd + 5 * npa; c->P.uy = pd + 6 * npa; c->P.omega = pd + 7 * npa;
     c->P.theta = pd + 8 * npa; c->P.rho_s = pd + 9 * npa;
     c->P.xf[0] = pf; c->P.xf[1] = pf + npa; c->P.yf[0] = pf + 2 * npa; c->P.yf[1] = pf + 3 * npa;
+    if (c->strip) {
+        // exchange buffers: 9 plane rows each, GUARD readable elements around
+        const size_t row_elems = 9 * (size_t)L.pitch + 2 * (size_t)GUARD;
+        for (int k = 0; k < 4; ++k) {
+            void *q = nullptr;
+            cudaError_t e2 = cudaMalloc(&q, row_elems * c->elem);
+            if (e2 != cudaSuccess) return bail(cuda_fail(e2, "cudaMalloc halo rows"));
+            c->owned[c->nowned++] = q;
+            e2 = cudaMemsetAsync(q, 0, row_elems * c->elem, c->stream);
+            if (e2 != cudaSuccess) return bail(cuda_fail(e2, "cudaMemsetAsync"));
+            (k < 2 ? c->xsend[k] : c->xrecv[k - 2]) = static_cast<char *>(q) + GUARD * c->elem;
+        }
+        if ((rc = dev_alloc(c, &c->fpart, 5 * (size_t)npa))) return bail(rc);
+        if (L.side_kind[SOUTH] == SIDE_HALO) L.halo[0] = c->xrecv[0];
+        if (L.side_kind[NORTH] == SIDE_HALO) L.halo[1] = c->xrecv[1];
+    }
     cudaError_t e;
     if ((e = cudaMemsetAsync(c->err, 0, sizeof(int), c->stream)) != cudaSuccess ||
         (e = cudaMemsetAsync(c->force, 0, sizeof(double) * 3 * npa, c->stream)) != cudaSuccess ||
@@ -673,15 +724,99 @@ int dilbm_create(const dilbm_grid *g, dilbm_lattice lattice, double tau, double 
     }
     if ((e = cudaGetLastError()) != cudaSuccess) return bail(cuda_fail(e, "init_kernel"));
     c->launches += 1;
+    for (int k = 0; k < 2 && c->strip; ++k) {
+        // the neighbours' rows start in the same uniform state
+        Lattice Lh = L;
+        Lh.ny = 1;
+        Lh.plane = L.pitch;
+        switch (c->storage) {
+        case DILBM_FP32: init_kernel<float><<<64, 256, 0, c->stream>>>((float *)c->xrecv[k], Lh, drho, u0x, u0y); break;
+        case DILBM_FP16_DEV: init_kernel<__half><<<64, 256, 0, c->stream>>>((__half *)c->xrecv[k], Lh, drho, u0x, u0y); break;
+        default: init_kernel<__nv_bfloat16><<<64, 256, 0, c->stream>>>((__nv_bfloat16 *)c->xrecv[k], Lh, drho, u0x, u0y); break;
+        }
+        if ((e = cudaGetLastError()) != cudaSuccess) return bail(cuda_fail(e, "init_kernel"));
+        c->launches += 1;
+    }
     if (np > 0 && (rc = upload_particles(c, particles, np))) return bail(rc);
     if ((e = cudaStreamSynchronize(c->stream)) != cudaSuccess) return bail(cuda_fail(e, "cudaStreamSynchronize"));
     *out = c;
     return DILBM_OK;
 }
 
+extern "C" {
+
+int dilbm_create(const dilbm_grid *g, dilbm_lattice lattice, double tau, double interface_width,
+                 const dilbm_particle *particles, int np, void *cuda_stream, dilbm_ctx **out) {
+    const dilbm::TraceRange trace("dilbm_create");
+    if (!g || !out) return fail(DILBM_ERR_INVALID_ARG, "grid and out must not be NULL");
+    *out = nullptr;
+    return create_ctx(g, lattice, tau, interface_width, particles, np, cuda_stream, 0, g->ny, out);
+}
+
+int dilbm_create_strip(const dilbm_grid *g, dilbm_lattice lattice, double tau, double interface_width,
+                       const dilbm_particle *particles, int np, int y0, int y1, void *cuda_stream,
+                       dilbm_ctx **out) {
+    const dilbm::TraceRange trace("dilbm_create_strip");
+    if (!g || !out) return fail(DILBM_ERR_INVALID_ARG, "grid and out must not be NULL");
+    *out = nullptr;
+    if (y0 < 0 || y1 > g->ny || y1 - y0 < 2 || (y0 == 0 && y1 == g->ny))
+        return fail(DILBM_ERR_INVALID_ARG, "a strip holds rows [y0, y1) with 0 <= y0, y1 <= ny, at least two rows "
+                                           "and not the whole lattice");
+    if (y0 % TILE_H != 0 || (y1 % TILE_H != 0 && y1 != g->ny))
+        return fail(DILBM_ERR_INVALID_ARG, "strip cuts must lie on multiples of " + std::to_string(TILE_H) + " rows");
+    if (g->south.kind == DILBM_SIDE_PERIODIC && np > 0) {
+        double rmax = 0.0;
+        for (int k = 0; k < np && particles; ++k) rmax = particles[k].r > rmax ? particles[k].r : rmax;
+        const double reach = 2.0 * (rmax + dilbm::reach_cut(g->method, interface_width)) + 2.0;
+        if (g->ny < reach + TILE_H)
+            return fail(DILBM_ERR_INVALID_ARG, "a periodic y axis this short for its discs is not split into strips");
+    }
+    return create_ctx(g, lattice, tau, interface_width, particles, np, cuda_stream, y0, y1, out);
+}
+
+int dilbm_strip_begin(dilbm_ctx *c) {
+    const dilbm::TraceRange trace("dilbm_strip_begin");
+    if (!c || !c->strip || c->strip_open) return fail(DILBM_ERR_INVALID_ARG, "not a strip, or a step already begun");
+    int rc = launch_sweep<MODE_STEP>(c, c->buf[c->cur], c->buf[c->cur ^ 1], FieldsOut{});
+    if (rc) return rc;
+    if (c->np > 0 && (rc = launch_particles(c, 1, 1))) return rc;
+    // this strip's first and last rows of every plane, for the neighbours
+    const size_t pitch_b = (size_t)c->L.pitch * c->elem, plane_b = (size_t)c->L.plane * c->elem;
+    const char *dst = static_cast<const char *>(c->buf[c->cur ^ 1]);
+    DILBM_CUDA(cudaMemcpy2DAsync(c->xsend[0], pitch_b, dst, plane_b, pitch_b, 9, cudaMemcpyDeviceToDevice, c->stream));
+    DILBM_CUDA(cudaMemcpy2DAsync(c->xsend[1], pitch_b, dst + (size_t)(c->L.ny - 1) * pitch_b, plane_b, pitch_b, 9,
+                                 cudaMemcpyDeviceToDevice, c->stream));
+    c->strip_open = true;
+    return DILBM_OK;
+}
+
+int dilbm_strip_end(dilbm_ctx *c) {
+    const dilbm::TraceRange trace("dilbm_strip_end");
+    if (!c || !c->strip || !c->strip_open) return fail(DILBM_ERR_INVALID_ARG, "not a strip, or no step begun");
+    int rc;
+    if (c->np > 0 && (rc = launch_particles(c, 1, 2))) return rc;
+    c->cur ^= 1;
+    c->fsum_steps += 1;
+    c->strip_open = false;
+    return DILBM_OK;
+}
+
+int dilbm_strip_buffers(dilbm_ctx *c, double **fpart, void **send_south, void **send_north, void **recv_south,
+                        void **recv_north, long long *row_elems) {
+    if (!c || !c->strip) return fail(DILBM_ERR_INVALID_ARG, "not a strip");
+    if (fpart) *fpart = c->fpart;
+    if (send_south) *send_south = c->xsend[0];
+    if (send_north) *send_north = c->xsend[1];
+    if (recv_south) *recv_south = c->xrecv[0];
+    if (recv_north) *recv_north = c->xrecv[1];
+    if (row_elems) *row_elems = 9LL * c->L.pitch;
+    return DILBM_OK;
+}
+
 int dilbm_step(dilbm_ctx *c, long long nsteps) {
     const dilbm::TraceRange trace("dilbm_step");
     if (!c || nsteps < 0) return fail(DILBM_ERR_INVALID_ARG, "bad context or step count");
+    if (c->strip) return fail(DILBM_ERR_INVALID_ARG, "a strip steps through dilbm_strip_begin / dilbm_strip_end");
     // whole step pairs replay a captured graph (timing brackets every sweep
     // launch with events instead; a stream the caller is capturing gets the
     // launches themselves)
@@ -758,6 +893,7 @@ int dilbm_force_mean(dilbm_ctx *c, double *mean, long long *nsteps) {
 
 int dilbm_set_moving_frame(dilbm_ctx *c, int particle, double x_ref) {
     if (!c) return fail(DILBM_ERR_INVALID_ARG, "NULL context");
+    if (c->strip && particle >= 0) return fail(DILBM_ERR_INVALID_ARG, "moving frame: not on a strip");
     if (particle < -1 || particle >= c->np)
         return fail(DILBM_ERR_INVALID_ARG, "moving frame: particle index out of range");
     if (particle >= 0 && !std::isfinite(x_ref)) return fail(DILBM_ERR_INVALID_ARG, "moving frame: x_ref not finite");
@@ -1121,6 +1257,8 @@ int dilbm_batch_create(dilbm_ctx *const *members, int n, void *cuda_stream, dilb
             return fail(DILBM_ERR_INVALID_ARG, "all members of a batch must use the same storage");
         if (members[k]->method != DILBM_METHOD_DI)
             return fail(DILBM_ERR_INVALID_ARG, "batches advance DI-LBM contexts only");
+        if (members[k]->strip)
+            return fail(DILBM_ERR_INVALID_ARG, "a strip of a decomposed lattice cannot join a batch");
         if (members[k]->track >= 0)
             return fail(DILBM_ERR_INVALID_ARG, "batches advance fixed-frame contexts only");
         for (int j = 0; j < k; ++j)

@@ -183,7 +183,8 @@ int dilbm_server_create(const dilbm_server_config *cfg, void *cuda_stream, dilbm
     (void)cuda_stream;       // every job runs on a stream of its own
     if (!cfg || !out) return sfail(DILBM_ERR_INVALID_ARG, "config and out must not be NULL");
     *out = nullptr;
-    if (cfg->storage != DILBM_STORAGE_PER_JOB && (cfg->storage < DILBM_FP32 || cfg->storage > DILBM_BF16_DEV))
+    if (cfg->storage != DILBM_STORAGE_PER_JOB && cfg->storage != DILBM_STORAGE_AUTO &&
+        (cfg->storage < DILBM_FP32 || cfg->storage > DILBM_BF16_DEV))
         return sfail(DILBM_ERR_INVALID_ARG, "unknown storage");
     if (cfg->max_jobs < 1 || cfg->max_jobs > MAX_JOBS)
         return sfail(DILBM_ERR_INVALID_ARG, "max_jobs must be 1.." + std::to_string(MAX_JOBS));
@@ -201,6 +202,8 @@ int dilbm_server_create(const dilbm_server_config *cfg, void *cuda_stream, dilbm
     }
     dilbm_server *s = new dilbm_server();
     s->cfg = *cfg;
+    if (!(s->cfg.auto_tau_max > 0.0)) s->cfg.auto_tau_max = 0.6;
+    if (!(s->cfg.auto_area_max > 0.0)) s->cfg.auto_area_max = 0.05;
     s->budget = budget;
     s->t0 = std::chrono::steady_clock::now();
     *out = s;
@@ -213,7 +216,15 @@ int dilbm_server_submit(dilbm_server *s, const dilbm_job *job, long long *id) {
     if (job->mean_window < 0 || job->mean_window > job->nsteps)
         return sfail(DILBM_ERR_INVALID_ARG, "mean_window must be 0..nsteps");
     dilbm_grid g = job->grid;
-    if (s->cfg.storage != DILBM_STORAGE_PER_JOB) g.storage = s->cfg.storage;
+    if (s->cfg.storage == DILBM_STORAGE_AUTO) {
+        double area = 0.0;
+        for (int k = 0; k < job->np && job->particles; ++k)
+            area += 3.14159265358979323846 * job->particles[k].r * job->particles[k].r;
+        const double frac = area / ((double)g.nx * (double)g.ny);
+        g.storage = (job->tau > s->cfg.auto_tau_max || frac > s->cfg.auto_area_max) ? DILBM_FP32 : DILBM_FP16_DEV;
+    } else if (s->cfg.storage != DILBM_STORAGE_PER_JOB) {
+        g.storage = s->cfg.storage;
+    }
     int rc = dilbm::check_problem(&g, DILBM_D2Q9, job->tau, job->interface_width, job->particles, job->np);
     if (rc) return rc;
     if (g.method != DILBM_METHOD_DI) return sfail(DILBM_ERR_INVALID_ARG, "the server runs DI-LBM jobs only");
@@ -358,6 +369,7 @@ int dilbm_server_status(const dilbm_server *s, long long id, dilbm_job_status *s
     st->admitted = j.admitted;
     st->finished = j.finished;
     st->footprint = j.footprint;
+    st->storage = j.grid.storage;
     return DILBM_OK;
 }
 

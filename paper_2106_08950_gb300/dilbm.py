@@ -29,6 +29,7 @@ MAX_CANDIDATES = 32
 FP32, FP16_DEV, BF16_DEV = 0, 1, 2
 STORAGE = {"fp32": FP32, "fp16": FP16_DEV, "bf16": BF16_DEV}
 STORAGE_PER_JOB = -1          # server: each job keeps its own storage
+STORAGE_AUTO = -2             # server: FP16 where the job's tau and disc area allow, else FP32
 SIDE = {W.PERIODIC: 0, W.VELOCITY: 1, W.PRESSURE: 2}
 
 
@@ -58,7 +59,8 @@ class Particle(C.Structure):
 
 class ServerConfig(C.Structure):
     _fields_ = [("storage", C.c_int), ("max_jobs", C.c_int), ("macro_steps", C.c_longlong),
-                ("memory_budget", C.c_double), ("policy", C.c_int)]
+                ("memory_budget", C.c_double), ("policy", C.c_int),
+                ("auto_tau_max", C.c_double), ("auto_area_max", C.c_double)]
 
 
 class Job(C.Structure):
@@ -70,7 +72,7 @@ class Job(C.Structure):
 class JobStatus(C.Structure):
     _fields_ = [("state", C.c_int), ("error", C.c_int), ("np", C.c_int), ("steps_done", C.c_longlong),
                 ("arrival", C.c_double), ("admitted", C.c_double), ("finished", C.c_double),
-                ("footprint", C.c_ulonglong)]
+                ("footprint", C.c_ulonglong), ("storage", C.c_int)]
 
 
 class ServerStats(C.Structure):
@@ -145,6 +147,11 @@ def load_library(path: Optional[str] = None):
     L.dilbm_frame_offset.argtypes = [vp, C.POINTER(C.c_longlong)]
     L.dilbm_server_clock.argtypes = [vp]
     L.dilbm_server_clock.restype = C.c_double
+    L.dilbm_create_strip.argtypes = [C.POINTER(Grid), ip, C.c_double, C.c_double, C.POINTER(Particle), ip, ip, ip,
+                                     vp, C.POINTER(vp)]
+    L.dilbm_strip_begin.argtypes = [vp]
+    L.dilbm_strip_end.argtypes = [vp]
+    L.dilbm_strip_buffers.argtypes = [vp] + [C.POINTER(vp)] * 5 + [C.POINTER(C.c_longlong)]
     L.dilbm_server_destroy.argtypes = [vp]
     L.dilbm_server_destroy.restype = None
     for name in ("dilbm_create", "dilbm_step", "dilbm_forces", "dilbm_fields", "dilbm_get_populations",
@@ -154,7 +161,8 @@ def load_library(path: Optional[str] = None):
                  "dilbm_server_create", "dilbm_server_submit", "dilbm_server_progress", "dilbm_server_status",
                  "dilbm_server_result", "dilbm_force_mean", "dilbm_force_mean_reset", "dilbm_autotune",
                  "dilbm_set_shape", "dilbm_batch_autotune", "dilbm_batch_set_shape", "dilbm_set_moving_frame",
-                 "dilbm_frame_offset", "dilbm_wait_probe"):
+                 "dilbm_frame_offset", "dilbm_wait_probe", "dilbm_create_strip", "dilbm_strip_begin",
+                 "dilbm_strip_end", "dilbm_strip_buffers"):
         getattr(L, name).restype = C.c_int
     if path == LIB_PATH:
         _lib = L
@@ -241,15 +249,19 @@ class Simulation:
         self.prob = prob
         self.storage = storage
         self.np = len(prob.particles)
+        self.ny = prob.ny                # rows held (a strip holds fewer)
         if stream is None:
             stream = current_stream_handle()
         self.stream = stream
         self._grid = make_grid(prob, storage)
         self._parts = make_particles(prob.particles)
         h = C.c_void_p()
-        check(self.L.dilbm_create(C.byref(self._grid), 0, prob.tau, prob.eps, self._parts, self.np,
-                                  C.c_void_p(stream), C.byref(h)))
+        check(self._create(h))
         self.h = h
+
+    def _create(self, h) -> int:
+        return self.L.dilbm_create(C.byref(self._grid), 0, self.prob.tau, self.prob.eps, self._parts, self.np,
+                                   C.c_void_p(self.stream), C.byref(h))
 
     # -- lifetime
     def close(self) -> None:
@@ -316,7 +328,7 @@ class Simulation:
 
     def fields(self):
         """rho, ux, uy, phi as (ny, nx) float32 host arrays."""
-        sh = (self.prob.ny, self.prob.nx)
+        sh = (self.ny, self.prob.nx)
         out = [np.empty(sh, dtype=np.float32) for _ in range(4)]
         check(self.L.dilbm_fields(self.h, *[o.ctypes.data for o in out], 0))
         return tuple(out)
@@ -328,13 +340,13 @@ class Simulation:
         check(self.L.dilbm_fields(self.h, *ptr, 1))
 
     def populations(self) -> np.ndarray:
-        out = np.empty((9, self.prob.ny, self.prob.nx))
+        out = np.empty((9, self.ny, self.prob.nx))
         check(self.L.dilbm_get_populations(self.h, out.ctypes.data))
         return out
 
     def set_populations(self, f: np.ndarray) -> None:
         f = np.ascontiguousarray(f, dtype=np.float64)
-        assert f.size == 9 * self.prob.nx * self.prob.ny
+        assert f.size == 9 * self.prob.nx * self.ny
         check(self.L.dilbm_set_populations(self.h, f.ctypes.data))
 
     def set_particles(self, parts) -> None:
@@ -369,6 +381,39 @@ class Simulation:
     @property
     def launches(self) -> int:
         return int(self.L.dilbm_launch_count(self.h))
+
+
+class Strip(Simulation):
+    """Rows [y0, y1) of a lattice split over ranks (``dilbm_create_strip``).
+    A step is ``begin()``, the caller's exchange of halo rows and force sums
+    (see ``strips.py``), then ``end()``; ``buffers()`` gives the device
+    addresses the exchange reads and writes."""
+
+    def __init__(self, prob: W.Problem, y0: int, y1: int, storage: str = "fp32", stream: Optional[int] = None):
+        self.y0, self.y1 = int(y0), int(y1)
+        super().__init__(prob, storage, stream)
+        self.ny = self.y1 - self.y0
+
+    def _create(self, h) -> int:
+        return self.L.dilbm_create_strip(C.byref(self._grid), 0, self.prob.tau, self.prob.eps, self._parts,
+                                         self.np, self.y0, self.y1, C.c_void_p(self.stream), C.byref(h))
+
+    def step(self, n: int = 1) -> None:
+        raise DilbmError(ERR_INVALID_ARG, "a strip steps through begin(), the exchange and end()")
+
+    def begin(self) -> None:
+        check(self.L.dilbm_strip_begin(self.h))
+
+    def end(self) -> None:
+        check(self.L.dilbm_strip_end(self.h))
+
+    def buffers(self):
+        """Device addresses: fpart (np x 5 doubles), send_south, send_north,
+        recv_south, recv_north (row_elems stored elements each), row_elems."""
+        p = [C.c_void_p() for _ in range(5)]
+        n = C.c_longlong()
+        check(self.L.dilbm_strip_buffers(self.h, *[C.byref(q) for q in p], C.byref(n)))
+        return tuple(q.value for q in p) + (int(n.value),)
 
 
 class Batch:
@@ -435,8 +480,9 @@ class Server:
                  memory_budget: float = 0.0, policy: int = ADMIT_FIFO):
         self.L = load_library()
         self.storage = storage
-        code = STORAGE_PER_JOB if storage == "per_job" else STORAGE[storage]
-        cfg = ServerConfig(code, int(max_jobs), int(macro_steps), float(memory_budget), int(policy))
+        code = {"per_job": STORAGE_PER_JOB, "auto": STORAGE_AUTO}.get(storage, None)
+        code = STORAGE[storage] if code is None else code
+        cfg = ServerConfig(code, int(max_jobs), int(macro_steps), float(memory_budget), int(policy), 0.0, 0.0)
         h = C.c_void_p()
         check(self.L.dilbm_server_create(C.byref(cfg), None, C.byref(h)))
         self.h = h
