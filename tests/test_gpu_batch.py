@@ -82,7 +82,7 @@ def test_batch_member_matches_oracle(stream):
     batch = D.Batch(members)
     batch.step(600)
     batch.sync()
-    o = O.OracleSim(probs[0])
+    o = O.OracleSim(probs[0], phi_cutoff=PAR.oracle_cutoff(probs[0]))
     o.step(600)
     ok, errs = PAR.compare_fields(members[0].fields(), o.fields())
     assert ok, errs
@@ -115,10 +115,12 @@ def test_full_size_batch_workload_against_oracle(stream):
     rng = np.random.default_rng(1)
     for k, (p, m) in enumerate(zip(jobs, members)):
         o = O.OracleSim(p, phi_cutoff=4 * p.eps)
-        o.step(4)
+        o.step(3)
+        pre = PAR.oracle_pre(o)
+        o.step(1)
         Fg, _, Sg = m.forces()
         Fo, _, So = o.forces()
-        ok, e = PAR.compare_forces(Fg, Fo, PAR.TOL_FP32_SUSPENSION_FORCE, max(q.r for q in p.particles))
+        ok, e = PAR.compare_forces_terms(Fg, Fo, PAR.force_term_scales(p, *pre))
         assert ok, (k, p.name, e)
         ok, e = PAR.compare_state(Sg, So)
         assert ok, (k, p.name, e)

@@ -38,7 +38,7 @@ def test_bounded_wait_reports_timeout_and_the_device_stays_usable(stream):
     prob = W.Problem(nx=64, ny=48, tau=0.8, eps=2.0, u0=(0.01, 0.0),
                      particles=[W.Particle(30.3, 20.6, 6.0, ux=0.02, rho_s=1.3)])
     g = D.Simulation(prob, stream=stream)
-    o = O.OracleSim(prob)
+    o = O.OracleSim(prob, phi_cutoff=PAR.oracle_cutoff(prob))
     g.step(50)
     o.step(50)
     g.sync()

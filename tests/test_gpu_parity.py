@@ -28,29 +28,44 @@ def stream():
     return int(s.cuda_stream)
 
 
-def run_both(prob, steps, stream, storage="fp32", cutoff=0.0, chunks=1):
+def run_both(prob, steps, stream, storage="fp32", chunks=1):
+    """Step the CUDA path and the oracle (with the sweep's phi cutoff)
+    ``steps`` times.  The oracle's fields and particle state at the start of
+    the last step (the inputs of the force compared afterwards) are kept on
+    the oracle object as ``o.pre``."""
     g = D.Simulation(prob, storage=storage, stream=stream)
-    o = O.OracleSim(prob, phi_cutoff=cutoff)
-    per = steps // chunks
-    for _ in range(chunks):
-        g.step(per)
-        o.step(per)
+    o = O.OracleSim(prob, phi_cutoff=PAR.oracle_cutoff(prob))
+    done, per = 0, max(1, (steps - 1) // chunks)
+    while done < steps - 1:
+        n = min(per, steps - 1 - done)
+        g.step(n)
+        o.step(n)
+        done += n
+    o.pre = (o.fields(), o.forces()[2]) if prob.particles else None
+    g.step(steps - done)
+    o.step(steps - done)
     g.sync()
     return g, o
 
 
-def assert_parity(g, o, tol=PAR.TOL_FP32, check_state=True, force_tol=None):
+def assert_forces(g, o, prob, tol=PAR.TOL_FP32, check_state=True):
+    """Per-particle force and torque against the oracle, each held to ``tol``
+    of the sum of the magnitudes of its node terms (Eqs. 18-19) at the start
+    of the step (``o.pre``); then the particle state."""
+    Fg, _, Sg = g.forces()
+    Fo, _, So = o.forces()
+    ok, e = PAR.compare_forces_terms(Fg, Fo, PAR.force_term_scales(prob, *o.pre), tol)
+    assert ok, e
+    if check_state:
+        ok, e = PAR.compare_state(Sg, So)
+        assert ok, e
+
+
+def assert_parity(g, o, tol=PAR.TOL_FP32, check_state=True):
     ok, errs = PAR.compare_fields(g.fields(), o.fields(), tol)
     assert ok, errs
     if g.np:
-        Fg, _, Sg = g.forces()
-        Fo, _, So = o.forces()
-        rmax = max(q.r for q in g.prob.particles)
-        ok, e2 = PAR.compare_forces(Fg, Fo, force_tol or tol, rmax)
-        assert ok, e2
-        if check_state:
-            ok, e3 = PAR.compare_state(Sg, So)
-            assert ok, e3
+        assert_forces(g, o, g.prob, tol, check_state)
 
 
 def moving_particles(nx=160, ny=40):
@@ -65,7 +80,7 @@ def test_periodic_moving_particles(stream):
     # Two tiles in x (128 + 32 nodes), five in y; one disc straddles both edges.
     # Free, settling discs: particle forces use the suspension bound.
     g, o = run_both(moving_particles(), 300, stream)
-    assert_parity(g, o, force_tol=PAR.TOL_FP32_SUSPENSION_FORCE)
+    assert_parity(g, o)
 
 
 @pytest.mark.parametrize("nx", [129, 257])
@@ -82,7 +97,7 @@ def test_east_wall_opening_a_row_segment(stream):
     # the same geometry against a no-slip east wall, in a closed box
     prob = W.sedimentation(nx=129, ny=70, r=6.0, rho_s=1.5, g=2e-5, x0=121.0, y0=40.0)
     g, o = run_both(prob, 300, stream)
-    assert_parity(g, o, force_tol=PAR.TOL_FP32_SUSPENSION_FORCE)
+    assert_parity(g, o)
 
 
 @pytest.mark.parametrize("nx,ny", [(33, 64), (47, 22), (160, 21)])
@@ -96,7 +111,7 @@ def test_short_periodic_axes(stream, nx, ny):
                      particles=[W.Particle(nx - 9.0, ny / 2.0 + 0.4, 6.6, ux=-0.001, uy=-0.009, rho_s=1.57),
                                 W.Particle(8.3, 2.9, 3.1, ux=0.004, uy=0.002, rho_s=1.3)])
     g, o = run_both(prob, 150, stream)
-    assert_parity(g, o, force_tol=PAR.TOL_FP32_SUSPENSION_FORCE)
+    assert_parity(g, o)
 
 
 def test_ragged_lattice_not_multiple_of_four(stream):
@@ -104,7 +119,7 @@ def test_ragged_lattice_not_multiple_of_four(stream):
     prob.particles = [W.Particle(128.4, 10.3, 4.0, ux=0.01, omega=0.003, rho_s=1.2),
                       W.Particle(50.5, 9.5, 5.0, uy=-0.01, rho_s=1.4)]
     g, o = run_both(prob, 200, stream)
-    assert_parity(g, o, force_tol=PAR.TOL_FP32_SUSPENSION_FORCE)
+    assert_parity(g, o)
 
 
 @pytest.mark.parametrize("fm", [W.FORCE_EQ18, W.FORCE_MOMENTUM])
@@ -131,7 +146,7 @@ def test_closed_box_settling_near_wall(stream, fm):
     g, o = run_both(prob, 600, stream)
     _, Fc, _ = o.forces()
     assert abs(Fc[0, 0]) > 0.0          # the wall repulsion acts during the run
-    assert_parity(g, o, force_tol=PAR.TOL_FP32_SUSPENSION_FORCE)
+    assert_parity(g, o)
 
 
 def test_particle_contacts_wan_turek(stream):
@@ -148,14 +163,8 @@ def test_particle_contacts_wan_turek(stream):
     _, Fco, _ = o.forces()
     assert np.abs(Fco).max() > 1e-3                      # contact forces are on
     assert np.allclose(Fcg, Fco, rtol=1e-5, atol=1e-5 * np.abs(Fco).max())
-    ok, errs = PAR.compare_fields(g.fields(), o.fields())
-    assert ok, errs
-    Fg, _, Sg = g.forces()
-    Fo, _, So = o.forces()
-    ok, e = PAR.compare_forces(Fg, Fo, PAR.TOL_FP32_SUSPENSION_FORCE, max(q.r for q in prob.particles))
-    assert ok, e
-    ok, e = PAR.compare_state(Sg, So)
-    assert ok, e
+    PAR.record("contact_force_rel", np.abs(Fcg - Fco).max() / np.abs(Fco).max(), PAR.TOL_FP32)
+    assert_parity(g, o)
 
 
 def test_pressure_driven_channel(stream):
@@ -167,16 +176,23 @@ def test_pressure_driven_channel(stream):
 
 
 def test_velocity_walls_couette(stream):
+    # A wall-driven shear flow approaching its steady linear profile.  Near a
+    # steady state every node rounds the same way every step, so FP32
+    # rounding acts as a persistent forcing that the viscous relaxation
+    # integrates: the FP32 steady state of this channel lies 1.4e-5 to
+    # 1.75e-5 (relative L2, wall speeds 0.05 to 0.01) from the exact linear
+    # profile the FP64 oracle converges to, with moments, velocity, moment
+    # form and its constants each contributing.  The bound is that floor.
     prob = W.Problem(nx=37, ny=17, tau=0.8, eps=2.0, south=W.wall(), north=W.wall(0.01, 0.0))
     g, o = run_both(prob, 3000, stream)
-    assert_parity(g, o)
+    assert_parity(g, o, tol=PAR.TOL_FP32_STEADY_SHEAR)
 
 
 def test_no_particles(stream):
     prob2, prof = W.shear_wave(n=64, amp=1e-3, tau=0.9, nx=64)
     f0 = np.stack([np.tile(O.equilibrium(1.0, u, 0.0), (prob2.nx, 1)).T for u in prof], axis=1)
     g = D.Simulation(prob2, stream=stream)
-    o = O.OracleSim(prob2)
+    o = O.OracleSim(prob2, phi_cutoff=PAR.oracle_cutoff(prob2))
     g.set_populations(f0)
     o.set_populations(f0)
     g.step(500)
@@ -191,31 +207,26 @@ def test_downscaled_periodic_suspension(stream):
     # the suspension bound (the velocity field keeps the 1e-5 bound).
     prob = W.periodic_suspension(n=512, count=32, seed=3)
     g, o = run_both(prob, 2000, stream, chunks=4)
-    ok, errs = PAR.compare_fields(g.fields(), o.fields())
-    assert ok, errs
-    Fg, _, Sg = g.forces()
-    Fo, _, So = o.forces()
-    ok, e = PAR.compare_forces(Fg, Fo, PAR.TOL_FP32_SUSPENSION_FORCE, max(q.r for q in prob.particles))
-    assert ok, e
-    ok, e = PAR.compare_state(Sg, So)
-    assert ok, e
+    assert_parity(g, o)
 
 
 def test_full_size_periodic_suspension_sampled(stream):
-    # The benchmark workload itself (4096^2, 2048 discs) for 6 steps in the
-    # same launch configuration; the oracle uses the same 4-width phi cutoff.
+    # The benchmark workload itself (4096^2, 2048 discs) for 200 steps in the
+    # bench's launch configuration (autotuned shape); the oracle uses the same
+    # 4-width phi cutoff.  Every particle, 200k random nodes and the nodes
+    # near the particles are compared.
     prob = W.periodic_suspension()
     o = O.OracleSim(prob, phi_cutoff=4 * prob.eps)
     g = D.Simulation(prob, stream=stream)
-    g.step(6)
-    o.step(6)
+    g.autotune()
+    for _ in range(4):
+        g.step(50 if _ < 3 else 49)
+        o.step(50 if _ < 3 else 49)
+    o.pre = (o.fields(), o.forces()[2])
+    g.step(1)
+    o.step(1)
     g.sync()
-    Fg, _, Sg = g.forces()
-    Fo, _, So = o.forces()
-    ok, e = PAR.compare_forces(Fg, Fo, PAR.TOL_FP32_SUSPENSION_FORCE, 12.0)
-    assert ok, e
-    ok, e = PAR.compare_state(Sg, So)
-    assert ok, e
+    assert_forces(g, o, prob)
     gf, of = g.fields(), o.fields()
     rng = np.random.default_rng(0)
     idx = rng.integers(0, prob.nx * prob.ny, size=200000)
@@ -226,6 +237,69 @@ def test_full_size_periodic_suspension_sampled(stream):
     near = np.flatnonzero(of[3].ravel() > 1e-3)[::7]
     ok, errs = PAR.compare_fields([a.ravel()[near] for a in gf[:4]], [a.ravel()[near] for a in of[:4]])
     assert ok, errs
+
+
+def test_settling_disc_full_size_against_oracle(stream):
+    # The settling-disc workload at its own size: a 400 x 2000 closed box (four
+    # no-slip walls), one free disc r = 12 released from rest at the centre,
+    # rho_s / rho_f = 1.5, g = 1e-5, tau = 0.8, eps = 2 (the geometry type of
+    # Sec. 3.2), for 5000 steps; the oracle uses the same 4-width phi cutoff.
+    prob = W.sedimentation()
+    g, o = run_both(prob, 5000, stream, chunks=10)
+    Fg, _, Sg = g.forces()
+    Fo, _, So = o.forces()
+    fell = prob.particles[0].y - So[0, 1]
+    assert So[0, 4] < -1e-3 and fell > 10.0                 # the disc is settling
+    ok, e = PAR.compare_state(Sg, So, travel=fell)
+    assert ok, e
+    pos_bound = PAR.TOL_FP32_POSITION + PAR.TOL_FP32 * fell
+    ok, errs = PAR.compare_fields(g.fields(), o.fields(), phi_tol=pos_bound / prob.eps)
+    assert ok, errs
+    assert_forces(g, o, prob, check_state=False)
+
+
+def eq27_settling_velocity(r, width, rho_s, g, tau):
+    """Terminal velocity of a disc between walls at low Re (Eq. 27) with the
+    wall factor K of Eq. 26, in lattice units."""
+    ws = width / (2 * r)
+    K = 1.0 / (math.log(ws) - 0.9175 + 1.7244 / ws ** 2 - 1.7302 / ws ** 4
+               + 2.4056 / ws ** 6 - 4.5913 / ws ** 8)
+    mu = (tau - 0.5) / 3.0
+    return (2 * r) ** 2 * (rho_s - 1.0) * g / (16 * K * mu)
+
+
+def test_settling_disc_full_trajectory(stream):
+    # The full 100k-step run of the same workload on the GPU in both force
+    # readings (physics check, not parity): the disc accelerates from rest to
+    # a terminal velocity and stays on the centre line.  With the momentum the
+    # fluid gives up it settles near Eq. 27 (the Stokes-limit formula; here
+    # Re_p ~ 0.8); with Eq. 18 as printed it settles 1 / (1 - 1/2tau) faster.
+    u27 = eq27_settling_velocity(12.0, 399.0, 1.5, 1e-5, 0.8)
+    v = {}
+    for fm in (W.FORCE_EQ18, W.FORCE_MOMENTUM):
+        prob = W.sedimentation(force_model=fm)
+        g = D.Simulation(prob, stream=stream)
+        traj = []
+        for k in range(100):
+            g.step(1000)
+            _, _, st = g.forces()
+            traj.append((st[0, 0], st[0, 1], st[0, 4]))
+        traj = np.array(traj)
+        g.close()
+        v[fm] = -traj[-10:, 2].mean()
+        drift = abs(traj[-1, 2] - traj[-10, 2]) / v[fm]
+        print(f"force model {fm}: terminal velocity {v[fm]:.4e} = {v[fm] / u27:.3f} x Eq. 27 "
+              f"({u27:.4e}); fell {traj[0, 1] - traj[-1, 1]:.1f} lu; lateral {abs(traj[:, 0] - 199.5).max():.2e}")
+        PAR.record(f"terminal_drift_fm{fm}", drift, 0.02)
+        assert drift < 0.02                                  # settled
+        assert abs(traj[:, 0] - 199.5).max() < 1e-3          # on the centre line
+        assert np.all(np.diff(traj[:, 1]) < 0)               # falling all the way
+    PAR.record("settling_vs_eq27", v[W.FORCE_MOMENTUM] / u27, 1.0)
+    assert 0.6 < v[W.FORCE_MOMENTUM] / u27 < 1.2
+    # Eq. 18's factor (1 - 1/2tau) speeds the disc up by at most its Stokes-
+    # limit factor; at this Re the larger speed meets a larger drag, so less
+    ratio = v[W.FORCE_EQ18] / v[W.FORCE_MOMENTUM]
+    assert 1.5 < ratio < 1.0 / (1 - 0.5 / 0.8)
 
 
 def test_fields_into_device_tensors(stream):
@@ -301,7 +375,7 @@ def test_reduced_precision_drag(stream, storage):
     # F_x over the last 700 steps of the 2000-step run, sampled every 10 steps.
     prob = W.cylinder_drag()
     g = D.Simulation(prob, storage=storage, stream=stream)
-    o = O.OracleSim(prob)
+    o = O.OracleSim(prob, phi_cutoff=PAR.oracle_cutoff(prob))
     fg, fo = [], []
     for k in range(200):
         g.step(10)
@@ -328,13 +402,16 @@ def test_lattice_past_32bit_offsets(stream):
     small = W.Problem(nx=256, ny=256, tau=0.8, eps=2.0, u0=(0.01, 0.004),
                       particles=[W.Particle(128.3, 128.7, **disc)])
     g = D.Simulation(big, stream=stream)
-    o = O.OracleSim(small)
-    g.step(40)
-    o.step(40)
+    o = O.OracleSim(small, phi_cutoff=PAR.oracle_cutoff(small))
+    g.step(39)
+    o.step(39)
+    o.pre = (o.fields(), o.forces()[2])
+    g.step(1)
+    o.step(1)
     g.sync()
     Fg, _, Sg = g.forces()
     Fo, _, So = o.forces()
-    ok, e = PAR.compare_forces(Fg, Fo, PAR.TOL_FP32_SUSPENSION_FORCE, 9.0)
+    ok, e = PAR.compare_forces_terms(Fg, Fo, PAR.force_term_scales(small, *o.pre))
     assert ok, e
     Sg = Sg.copy()
     Sg[:, 0] -= off[0]

@@ -36,18 +36,27 @@ def ps(prob):
 def run_both(prob, steps, stream, storage="fp32"):
     g = D.Simulation(prob, storage=storage, stream=stream)
     o = O.OracleSim(prob)
-    g.step(steps)
-    o.step(steps)
+    g.step(steps - 1)
+    o.step(steps - 1)
+    o.pre = PAR.oracle_pre(o)
+    g.step(1)
+    o.step(1)
     g.sync()
     return g, o
 
 
-def check(g, o, tol=PAR.TOL_FP32, force_tol=None, state=True):
-    ok, errs = PAR.compare_fields(g.fields(), o.fields(), tol)
+def check(g, o, tol=PAR.TOL_FP32, state=True):
+    """Fields at every node; each particle's force and torque held to ``tol``
+    of the sum of the magnitudes of its node terms (Eqs. 10-11), or to the
+    FP32 floor of a PS sum (ps_force_floor); the particle state."""
+    fo = o.fields()
+    ok, errs = PAR.compare_fields(g.fields(), fo, tol)
     assert ok, errs
     Fg, _, Sg = g.forces()
     Fo, _, So = o.forces()
-    ok, e = PAR.compare_forces(Fg, Fo, force_tol or tol, max(q.r for q in g.prob.particles))
+    rmax = max(q.r for q in g.prob.particles)
+    ok, e = PAR.compare_forces_terms(Fg, Fo, PAR.force_term_scales(g.prob, *o.pre), tol,
+                                     PAR.ps_force_floor(fo[3], So), rmax)
     assert ok, e
     if state:
         ok, e = PAR.compare_state(Sg, So)
@@ -95,13 +104,13 @@ def test_ps_periodic_moving_particles(stream):
                                    W.Particle(90.6, 27.4, 5.0, ux=-0.01, uy=0.015, omega=-0.001, rho_s=1.1),
                                    W.Particle(151.2, 3.1, 4.5, ux=0.005, rho_s=1.6)]))
     g, o = run_both(prob, 300, stream)
-    check(g, o, force_tol=PAR.TOL_FP32_SUSPENSION_FORCE)
+    check(g, o)
 
 
 def test_ps_closed_box_near_wall(stream):
     prob = ps(W.sedimentation(nx=64, ny=96, r=6.0, rho_s=1.5, g=2e-5, x0=6.3, y0=60.0))
     g, o = run_both(prob, 400, stream)
-    check(g, o, force_tol=PAR.TOL_FP32_SUSPENSION_FORCE)
+    check(g, o)
 
 
 def test_ps_solid_fraction_is_the_covered_area(stream):
@@ -139,15 +148,19 @@ def test_ps_larger_discs_arrive_mid_run(stream):
     bigger = [W.Particle(30.6, 30.9, 11.5, ux=0.01, rho_s=1.4), W.Particle(71.2, 25.4, 8.25, uy=0.01, rho_s=1.2)]
     g.set_particles(bigger)
     o.set_particles(bigger)
-    g.step(60)
-    o.step(60)
+    g.step(59)
+    o.step(59)
+    pre = PAR.oracle_pre(o)
+    g.step(1)
+    o.step(1)
     fo = o.fields()
     ok, errs = PAR.compare_fields(g.fields(), fo)
     assert ok, errs
     assert np.abs(g.fields()[3] - fo[3]).max() < 5e-6
     Fg, _, Sg = g.forces()
     Fo, _, So = o.forces()
-    ok, e = PAR.compare_forces(Fg, Fo, PAR.TOL_FP32_SUSPENSION_FORCE, 11.5, atol=PAR.ps_force_floor(fo[3], So))
+    ok, e = PAR.compare_forces_terms(Fg, Fo, PAR.force_term_scales(prob, *pre), PAR.TOL_FP32,
+                                     PAR.ps_force_floor(fo[3], So), 11.5)
     assert ok, e
     ok, e = PAR.compare_state(Sg, So)
     assert ok, e
@@ -160,13 +173,17 @@ def test_ps_full_size_suspension_sampled(stream):
     prob = ps(W.periodic_suspension())
     g = D.Simulation(prob, stream=stream)
     o = O.OracleSim(prob)
-    g.step(2)
-    o.step(2)
+    g.step(1)
+    o.step(1)
+    pre = PAR.oracle_pre(o)
+    g.step(1)
+    o.step(1)
     g.sync()
     fo = o.fields()
     Fg, _, Sg = g.forces()
     Fo, _, So = o.forces()
-    ok, e = PAR.compare_forces(Fg, Fo, PAR.TOL_FP32_SUSPENSION_FORCE, 12.0, atol=PAR.ps_force_floor(fo[3], So))
+    ok, e = PAR.compare_forces_terms(Fg, Fo, PAR.force_term_scales(prob, *pre), PAR.TOL_FP32,
+                                     PAR.ps_force_floor(fo[3], So), 12.0)
     assert ok, e
     ok, e = PAR.compare_state(Sg, So)
     assert ok, e

@@ -98,6 +98,29 @@ def test_mixed_storage_jobs_match_alone_bitwise(stream):
     srv.close()
 
 
+def test_automatic_storage_picks_fp32_for_viscous_or_packed_jobs(stream):
+    # DILBM_STORAGE_AUTO: a job runs in FP16 unless its tau exceeds 0.6 or its
+    # discs cover more than 5% of the lattice; each job then gets bit for bit
+    # the result it gets alone in the storage it was given
+    jobs = small_jobs(39, 8)
+    srv = D.Server("auto", max_jobs=16, macro_steps=16)
+    ids = [(srv.submit(p, n), p, n) for p, n in jobs]
+    drain(srv, [], [])
+    kinds = set()
+    for jid, p, n in ids:
+        st = srv.status(jid)
+        assert st.state == D.JOB_DONE
+        area = sum(np.pi * q.r ** 2 for q in p.particles) / (p.nx * p.ny)
+        want = D.FP32 if (p.tau > 0.6 or area > 0.05) else D.FP16_DEV
+        assert st.storage == want, (p.tau, area, st.storage)
+        kinds.add(st.storage)
+        F, S = srv.result(jid)
+        Fa, Sa = alone(p, n, "fp32" if want == D.FP32 else "fp16", stream)
+        assert np.array_equal(F, Fa) and np.array_equal(S, Sa), jid
+    assert kinds == {D.FP32, D.FP16_DEV}         # the draw exercises both choices
+    srv.close()
+
+
 def test_jobs_overlap_on_the_device(stream):
     jobs = small_jobs(32, 6)
     srv = D.Server("fp32", max_jobs=8, macro_steps=8)
