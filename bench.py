@@ -52,8 +52,12 @@ def parse():
     ap.add_argument("--e2e-steps", type=int, default=200)
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--cpu-table", action="store_true",
+                    help="time the oracle on 1 and all host cores for the cylinder, settling and suspension workloads")
     ap.add_argument("--requests", type=int, default=300, help="serve: leading requests of the stream")
     ap.add_argument("--max-jobs", type=int, default=64, help="serve: jobs resident at once")
+    ap.add_argument("--jobs-log", default=None,
+                    help="serve: write one JSON line per cylinder job (parameters, FP16 vs FP32 drag) to this file")
     ap.add_argument("--macro-steps", type=int, default=64, help="serve: steps per macro-step")
     ap.add_argument("--shape", default=None,
                     help="sweep launch shape warps,blocks_per_sm (default: the autotuner's)")
@@ -192,18 +196,66 @@ def barrier(dist):
 
 
 # ---------------------------------------------------------------- oracle arms
-def oracle_mlups(prob, seconds: float, max_steps: int = 1_000_000, min_steps: int = 2):
-    """Time the FP64 oracle as it stands on all host cores."""
+def force_model_name(fm: int) -> str:
+    return {0: "Eq. 18 as printed", 1: "momentum exchange"}.get(int(fm), str(fm))
+
+
+def cpu_model() -> str:
+    """The host CPU's model name (lscpu), for the oracle timings."""
+    import subprocess
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for line in out.splitlines():
+            if line.strip().lower().startswith("model name"):
+                return line.split(":", 1)[1].strip()
+    except (OSError, subprocess.SubprocessError):
+        pass
+    return "unknown"
+
+
+def oracle_mlups(prob, seconds: float, max_steps: int = 1_000_000, min_steps: int = 2, threads: int = 0):
+    """Time the FP64 oracle as it stands on the host cores (``threads``: 0 =
+    all of them)."""
     from oracle import oracle as O
-    sim = O.OracleSim(prob, phi_cutoff=4 * prob.eps)
-    sim.step(1)                      # warm-up: first-touch of the arrays
-    t0 = time.perf_counter()
-    n = 0
-    while n < max_steps and (n < min_steps or time.perf_counter() - t0 < seconds):
-        sim.step(1)
-        n += 1
-    dt = time.perf_counter() - t0
-    return prob.nx * prob.ny * n / dt / 1e6, n, dt, O.max_threads()
+    full = O.max_threads() if threads else 0
+    sim = O.OracleSim(prob, phi_cutoff=4 * prob.eps, threads=threads)
+    try:
+        sim.step(1)                      # warm-up: first-touch of the arrays
+        t0 = time.perf_counter()
+        n = 0
+        while n < max_steps and (n < min_steps or time.perf_counter() - t0 < seconds):
+            sim.step(1)
+            n += 1
+        dt = time.perf_counter() - t0
+        cores = O.max_threads()
+    finally:
+        sim.close()
+        if full:
+            O.set_threads(full)
+    return prob.nx * prob.ny * n / dt / 1e6, n, dt, cores
+
+
+def cpu_table(args):
+    """The oracle on the host cores, single-threaded and on every core, for
+    the cylinder workload in full (2000 steps), the settling disc (2000
+    steps) and the periodic suspension (20 steps); each measurement is capped
+    at --cpu-seconds x 10 of wall time and reports the steps it ran."""
+    from oracle import oracle as O
+    from paper_2106_08950_gb300 import workloads as W
+    cases = [("cylinder 200x100, r=10, Re=20", W.cylinder_drag(), 2000),
+             ("settling disc 400x2000, r=12", W.sedimentation(), 2000),
+             ("periodic suspension 4096x4096, 2048 discs", W.periodic_suspension(), 20)]
+    allc = O.max_threads()
+    rows = []
+    for name, prob, steps in cases:
+        for threads in (1, allc):
+            v, n, dt, cores = oracle_mlups(prob, args.cpu_seconds * 10, max_steps=steps, min_steps=1,
+                                           threads=threads)
+            rows.append({"workload": name, "threads": cores, "steps_run": n, "steps_asked": steps,
+                         "seconds": dt, "MLUPS": v})
+            print(json.dumps(rows[-1]), flush=True)
+    print(json.dumps({"cpu_table": rows, "cpu_model": cpu_model(), "cores": allc}), flush=True)
+    return 0
 
 
 def reference_arm(args):
@@ -367,6 +419,7 @@ def gpu_arm(args):
             "dtype": {"fp32": "f32", "fp16": "f16-storage/f32-math", "bf16": "bf16-storage/f32-math"}[args.storage],
             "data": "synthetic",
             "config": dict(cfg, storage=args.storage, nodes=nodes, particles=npart,
+                           force_model=force_model_name(prob.force_model),
                            launch_shape={"warps_per_block": shape[0], "blocks_per_sm": shape[1],
                                          "by": "--shape" if args.shape else "autotuner"},
                            l2="populations 9x2 planes exceed L2; no flush",
@@ -376,10 +429,14 @@ def gpu_arm(args):
     # ---- the oracle on the host cores, rank 0 at N=1 only
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         v, n, dt, cores = oracle_mlups(prob, args.cpu_seconds)
+        v1, n1, dt1, _ = oracle_mlups(prob, args.cpu_seconds, threads=1, min_steps=1)
         line["cpu_baseline"] = {"value": v, "unit": "MLUPS", "cores": cores, "kind": "oracle",
                                 "sample": f"{n} steps of the full workload ({dt:.1f} s), " + (
                                     "cell fractions within r + 0.71" if prob.method == W.METHOD_PS
-                                    else "phi cutoff 4 widths")}
+                                    else "phi cutoff 4 widths"),
+                                "single_thread": {"value": v1, "unit": "MLUPS", "cores": 1,
+                                                  "sample": f"{n1} steps of the full workload ({dt1:.1f} s)"},
+                                "cpu_model": cpu_model()}
     if rank == 0:
         print(json.dumps(line), flush=True)
     sim.close()
@@ -466,6 +523,7 @@ def batch_arm(args):
             "config": {"workload": "batch of 64 uneven lattices (seed 4): nx log-U[128,1024], ny log-U[128,2048], "
                                    "cylinder or sedimentation jobs, 1-32 discs r U[5,15], Re log-U[10,100]",
                        "storage": args.storage, "nodes": nodes, "nodes_all_ranks": total_nodes, "lattices": len(jobs),
+                       "force_model": ", ".join(sorted({force_model_name(j.force_model) for j in jobs})),
                        "particles": sum(len(j.particles) for j in jobs),
                        "launch": "one batched sweep + one batched particle launch per step, CUDA-graph replay",
                        "launch_shape": {"warps_per_block": shape[0], "blocks_per_sm": shape[1],
@@ -513,17 +571,19 @@ def replay_served(reqs, storage, args, D):
                 break
             time.sleep(max(0.0, reqs[nxt].arrival_s - (srv.clock() - t_base)))
     lat, res, first, last = {}, {}, None, 0.0
+    stored = {}
     for jid, k in ids.items():
         js = srv.status(jid)
         if js.state != D.JOB_DONE:
             raise RuntimeError(f"request {k} ended in state {js.state} (error {js.error})")
         lat[k] = js.finished - js.arrival
         last = max(last, js.finished - t_base)
+        stored[k] = js.storage
         res[k] = srv.result(jid, with_mean=True)
     first = reqs[0].arrival_s
     srv_stats = st
     srv.close()
-    return lat, res, last - first, srv_stats
+    return lat, res, last - first, srv_stats, stored
 
 
 def replay_single(reqs, storage, D, stream):
@@ -543,6 +603,27 @@ def replay_single(reqs, storage, D, stream):
         lat[k] = time.perf_counter() - t_base - r.arrival_s
         res[k] = (F, None, S)
     return lat, res, time.perf_counter() - t_base - reqs[0].arrival_s, launches
+
+
+def job_rows(reqs, res_a, res_b):
+    """Per cylinder job: its parameters and the FP16 (res_a) vs FP32 (res_b)
+    mean drag of its worst disc, for diagnosing the reduced-precision error."""
+    rows = []
+    for k, r in enumerate(reqs):
+        p = r.problem
+        if not p.particles or not p.particles[0].fixed:
+            continue
+        Fa, Fb = res_a[k][1], res_b[k][1]
+        u = abs(p.west.ux)
+        m = int(abs(Fa[:, 0] - Fb[:, 0]).argmax())
+        d = 2.0 * max(q.r for q in p.particles)
+        rows.append({"request": k, "name": p.name, "nx": p.nx, "ny": p.ny, "discs": len(p.particles),
+                     "steps": r.steps, "tau": p.tau, "U": u, "Re": u * d / ((p.tau - 0.5) / 3.0),
+                     "worst_disc": m, "r": p.particles[m].r, "x": p.particles[m].x,
+                     "Fx_fp16": float(Fa[m, 0]), "Fx_fp32": float(Fb[m, 0]),
+                     "max_abs_Fx_fp32": float(abs(Fb[:, 0]).max()),
+                     "cd_err": float(abs(Fa[m, 0] - Fb[m, 0]) / (0.5 * u * u * 2.0 * p.particles[m].r))})
+    return rows
 
 
 def drag_errors(reqs, res_a, res_b):
@@ -593,10 +674,10 @@ def serve_arm(args):
     clocks.start()
     time.sleep(0.3)
     barrier(dist)
-    for name, storage in (("served_fp16", "fp16"), ("served_fp32", "fp32")):
-        lat, res, span, st = replay_served(reqs, storage, args, D)
+    for name, storage in (("served_auto", "auto"), ("served_fp16", "fp16"), ("served_fp32", "fp32")):
+        lat, res, span, st, stored = replay_served(reqs, storage, args, D)
         span = max_over_ranks(dist, span, dev)
-        arms[name] = {"lat": lat, "res": res, "span": span, "launches": st.launches,
+        arms[name] = {"lat": lat, "res": res, "span": span, "launches": st.launches, "stored": stored,
                       "host": {"macro_steps": st.macro_steps, "busy_s": st.busy_seconds, "form_s": st.form_seconds,
                                "admit_s": st.admit_seconds, "wait_s": st.wait_seconds,
                                "retire_s": st.retire_seconds}}
@@ -615,39 +696,57 @@ def serve_arm(args):
             out["server_time"] = a["host"]
         return out
 
-    s16, s32, s1 = summary(arms["served_fp16"]), summary(arms["served_fp32"]), summary(arms["single_fp32"])
+    sa, s16, s32, s1 = (summary(arms["served_auto"]), summary(arms["served_fp16"]), summary(arms["served_fp32"]),
+                        summary(arms["single_fp32"]))
     d16, r16 = drag_errors(reqs, arms["served_fp16"]["res"], arms["served_fp32"]["res"])
+    if args.jobs_log:
+        with open(f"{args.jobs_log}.rank{rank}" if world > 1 else args.jobs_log, "w") as fh:
+            for row in job_rows(reqs, arms["served_fp16"]["res"], arms["served_fp32"]["res"]):
+                row["auto_storage"] = int(arms["served_auto"]["stored"][row["request"]])
+                fh.write(json.dumps(row) + "\n")
     d16, r16 = gather_lists(dist, d16), gather_lists(dist, r16)
+    da, ra = drag_errors(reqs, arms["served_auto"]["res"], arms["served_fp32"]["res"])
+    da, ra = gather_lists(dist, da), gather_lists(dist, ra)
+    n16 = sum_over_ranks(dist, sum(1 for v in arms["served_auto"]["stored"].values() if v == D.FP16_DEV), dev)
+    ncyl = sum_over_ranks(dist, sum(1 for k, r in enumerate(reqs) if r.problem.particles and r.problem.particles[0].fixed
+                                    and arms["served_auto"]["stored"][k] == D.FP16_DEV), dev)
     parts_in = sum(len(r.problem.particles) for r in reqs)
     import numpy as np
     same = all(np.array_equal(arms["served_fp32"]["res"][k][0], arms["single_fp32"]["res"][k][0]) and
                np.array_equal(arms["served_fp32"]["res"][k][2], arms["single_fp32"]["res"][k][2])
                for k in range(len(reqs)))
     same = sum_over_ranks(dist, 0.0 if same else 1.0, dev) == 0.0
-    line = {"metric": METRIC, "value": s16["value"], "unit": "MLUPS", "n_gpus": world, "steps": len(reqs),
+    def drag_summary(d, r):
+        return {"jobs": len(d), "quantity": "mean F_x over each cylinder job's last quarter of steps, vs served FP32",
+                "cd_units": {"median": percentile(d, 50), "p90": percentile(d, 90), "max": max(d) if d else None,
+                             "frac_le_1e-3": sum(1 for v in d if v <= 1e-3) / max(1, len(d))},
+                "relative": {"median": percentile(r, 50), "p90": percentile(r, 90), "max": max(r) if r else None,
+                             "frac_le_1e-3": sum(1 for v in r if v <= 1e-3) / max(1, len(r))}}
+
+    line = {"metric": METRIC, "value": sa["value"], "unit": "MLUPS", "n_gpus": world, "steps": len(reqs),
             "warmup": 1, "ms_per_step": None, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-            "dtype": "f16-storage/f32-math", "data": "synthetic",
+            "dtype": "f16/f32-storage (per job)/f32-math", "data": "synthetic",
             "config": {"workload": f"served: the first {len(reqs) * world} requests of a Poisson stream "
                                    "(seed 5, 50 requests/s): cylinder or sedimentation jobs, nx, ny log-U[128,2048], "
                                    "1-64 discs r U[5,15], steps log-U[1k,20k]; replayed in real time",
-                       "storage": "fp16", "node_updates": total_work, "max_jobs": args.max_jobs,
+                       "storage": "auto: FP16 deviations where tau <= 0.6 and the discs cover <= 5% of the "
+                                  "lattice, else FP32",
+                       "jobs_in_fp16": int(n16), "cylinder_jobs_in_fp16": int(ncyl),
+                       "node_updates": total_work, "max_jobs": args.max_jobs,
+                       "force_model": ", ".join(sorted({force_model_name(r.problem.force_model) for r in reqs})),
                        "macro_steps": args.macro_steps, "admission": "FIFO by job slots and free device memory",
                        "l2": "resident lattices exceed L2 once a few large jobs run; no flush",
                        "parallelism": f"replicas x{world}" if world > 1 else "single GPU"},
-            "latency": {"p50_s": s16["p50_s"], "p99_s": s16["p99_s"]},
-            "server_time": s16.get("server_time"),
-            "served_fp32": s32, "single_instance_fp32": s1,
-            "gain_over_single_fp32": {"mlups": s16["value"] / s1["value"], "p50": s1["p50_s"] / s16["p50_s"],
-                                      "p99": s1["p99_s"] / s16["p99_s"]},
-            "drag_error_fp16_vs_fp32": {
-                "jobs": len(d16), "quantity": "mean F_x over each cylinder job's last quarter of steps",
-                "cd_units": {"median": percentile(d16, 50), "p90": percentile(d16, 90), "max": max(d16) if d16 else None,
-                             "frac_le_1e-3": sum(1 for v in d16 if v <= 1e-3) / max(1, len(d16))},
-                "relative": {"median": percentile(r16, 50), "p90": percentile(r16, 90),
-                             "frac_le_1e-3": sum(1 for v in r16 if v <= 1e-3) / max(1, len(r16))}},
+            "latency": {"p50_s": sa["p50_s"], "p99_s": sa["p99_s"]},
+            "server_time": sa.get("server_time"),
+            "served_fp16_all_jobs": s16, "served_fp32": s32, "single_instance_fp32": s1,
+            "gain_over_single_fp32": {"mlups": sa["value"] / s1["value"], "p50": s1["p50_s"] / sa["p50_s"],
+                                      "p99": s1["p99_s"] / sa["p99_s"]},
+            "drag_error_auto_vs_fp32": drag_summary(da, ra),
+            "drag_error_fp16_all_jobs_vs_fp32": drag_summary(d16, r16),
             "fp32_served_equals_single_bitwise": same,
-            "roofline": None, "gpu_launches": s16["gpu_launches"],
-            "e2e": {"value": s16["value"], "unit": "MLUPS", "h2d_bytes_per_step": None, "d2h_bytes_per_step": None,
+            "roofline": None, "gpu_launches": sa["gpu_launches"],
+            "e2e": {"value": sa["value"], "unit": "MLUPS", "h2d_bytes_per_step": None, "d2h_bytes_per_step": None,
                     "h2d_bytes_per_request": parts_in * 72 // max(1, len(reqs)),
                     "d2h_bytes_per_request": parts_in * (72 + 24) // max(1, len(reqs)),
                     "note": "the served value is end to end: host job descriptions in, host results out"},
@@ -663,6 +762,8 @@ def main():
     args = parse()
     if args.impl == "reference":
         return reference_arm(args)
+    if args.cpu_table:
+        return cpu_table(args)
     if args.workload == "batch":
         return batch_arm(args)
     if args.workload == "serve":
