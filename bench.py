@@ -48,6 +48,9 @@ def parse():
     ap.add_argument("--method", default="di", choices=["di", "ps"],
                     help="coupling: the paper's DI-LBM, or its PS-LBM comparison (periodic/cylinder/sedimentation)")
     ap.add_argument("--size", type=int, default=4096, help="periodic box edge")
+    ap.add_argument("--decompose", action="store_true",
+                    help="periodic/settling workloads under torchrun: split one lattice into strips over the "
+                         "ranks (strong scaling) instead of one replica per rank")
     ap.add_argument("--particles", type=int, default=2048)
     ap.add_argument("--e2e-steps", type=int, default=200)
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
@@ -317,6 +320,58 @@ def measured_traffic(key):
                 if m.group(1) == key and m.group(3) == sha:
                     return int(m.group(2))
     return None
+
+
+def strips_arm(args):
+    """One lattice split into horizontal strips over the ranks (strong
+    scaling): each rank sweeps its rows and the ranks exchange the rows beside
+    each cut and the per-particle force sums every step (NCCL)."""
+    import torch
+    from paper_2106_08950_gb300 import strips as S
+
+    world, rank, local = dist_env()
+    torch.cuda.set_device(local)
+    dist = init_dist(world, "nccl")
+    dev = torch.device("cuda", local)
+    prob, cfg = make_problem(args, 0)               # the same lattice on every rank
+    stream = torch.cuda.Stream(device=dev)
+    sim = S.DecomposedSimulation(prob, storage=args.storage, stream=stream)
+    sim.step(args.warmup)
+    sim.sync()
+    clocks = ClockSampler(local)
+    clocks.start()
+    time.sleep(0.3)
+    barrier(dist)
+    torch.cuda.synchronize()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    l0 = sim.sim.launches
+    with torch.cuda.stream(stream):
+        ev0.record(stream)
+        sim.step(args.steps)
+        ev1.record(stream)
+    sim.sync()
+    torch.cuda.synchronize()
+    barrier(dist)
+    clk = clocks.stop()
+    ms = max_over_ranks(dist, ev0.elapsed_time(ev1), dev)
+    launches = int(sum_over_ranks(dist, sim.sim.launches - l0, dev))
+    value = prob.nx * prob.ny * args.steps / (ms / 1e3) / 1e6
+    line = {"metric": METRIC, "value": value, "unit": "MLUPS", "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
+            "scaling": "strong", "vs_baseline": None,
+            "dtype": {"fp32": "f32", "fp16": "f16-storage/f32-math", "bf16": "bf16-storage/f32-math"}[args.storage],
+            "data": "synthetic",
+            "config": dict(cfg, storage=args.storage, nodes=prob.nx * prob.ny, particles=len(prob.particles),
+                           force_model=force_model_name(prob.force_model),
+                           strips=[list(S.strip_rows(prob.ny, world, r)) for r in range(world)],
+                           l2="populations exceed L2; no flush", parallelism=f"strips x{world} (NCCL halo rows + "
+                                                                          "per-particle force all-reduce)"),
+            "roofline": None, "gpu_launches": launches, "e2e": None, "clocks": clk}
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    sim.close()
+    dist.destroy_process_group()
+    return 0
 
 
 def gpu_arm(args):
@@ -768,6 +823,8 @@ def main():
         return batch_arm(args)
     if args.workload == "serve":
         return serve_arm(args)
+    if args.decompose and dist_env()[0] > 1:
+        return strips_arm(args)
     return gpu_arm(args)
 
 
