@@ -505,9 +505,9 @@ class Server:
     def submit(self, prob: W.Problem, nsteps: int, arrival: float = -1.0, mean_window: int = 0,
                storage: Optional[str] = None) -> int:
         """Queue a job; ``storage`` picks its storage on a "per_job" server
-        (default "fp32") and is ignored otherwise."""
+        (default "fp32") and is ignored otherwise (an "auto" server picks it)."""
         parts = make_particles(prob.particles)
-        st = self.storage if self.storage != "per_job" else (storage or "fp32")
+        st = {"per_job": storage or "fp32", "auto": "fp32"}.get(self.storage, self.storage)
         job = Job(make_grid(prob, st), prob.tau, prob.eps, C.cast(parts, C.POINTER(Particle)),
                   len(prob.particles), int(nsteps), int(mean_window), float(arrival))
         jid = C.c_longlong()
