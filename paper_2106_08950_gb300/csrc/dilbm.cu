@@ -631,7 +631,7 @@ static int create_ctx(const dilbm_grid *g, dilbm_lattice lattice, double tau, do
     ph.omega = (float)(1.0 / tau);
     ph.kf = (float)(1.0 - 0.5 / tau);
     ph.kforce = g->force_model == DILBM_FORCE_EQ18 ? ph.kf : 1.0f;
-    ph.four_over_eps = (float)(4.0 / interface_width);
+    ph.phi_k2 = (float)(-4.0 / (interface_width * std::log(2.0)));
     ph.cut_d = dilbm::reach_cut(g->method, interface_width);
     ph.cut = (float)ph.cut_d;
     if (c->method == DILBM_METHOD_PS) {

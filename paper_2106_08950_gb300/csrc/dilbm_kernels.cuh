@@ -164,7 +164,7 @@ struct Physics {
     float omega;                // 1 / tau
     float kf;                   // 1 - 1/(2 tau): prefactor of F_i (Eq. 15)
     float kforce;               // kf (Eq. 18 as printed) or 1 (momentum exchange)
-    float four_over_eps;        // 4 / epsilon: phi = 1 / (1 + exp(-4 l / eps))
+    float phi_k2;               // -4 / (epsilon ln 2): phi = 1 / (1 + 2^(phi_k2 l)) = 1 / (1 + exp(-4 l / eps))
     float cut;                  // phi tail kept while l >= -cut
     int ck;                     // PS: half-width K of each particle's covered-area table (0: none)
     double cut_d;
@@ -708,6 +708,19 @@ __device__ __forceinline__ void staged_pull9(const Lattice &L, const T *stage, i
     if constexpr (I < 8) staged_pull9<T, I + 1>(L, stage, e, out);
 }
 
+// The hardware's base-2 exponential and reciprocal (PTX ex2.approx, rcp.approx;
+// subnormal results flush to zero, so 2^x for very negative x is 0).
+__device__ __forceinline__ float ex2_approx(float x) {
+    float r;
+    asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
+    return r;
+}
+__device__ __forceinline__ float rcp_approx(float x) {
+    float r;
+    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
+    return r;
+}
+
 // Slot m (0 or 1) of a node pair.
 __device__ __forceinline__ float &slot(float2 &v, int m) { return m ? v.y : v.x; }
 
@@ -893,8 +906,12 @@ __device__ __forceinline__ bool sweep_segment(const SweepArgs<T> &A, int y, int 
                     if (d2 > R * R) continue;
                     const float l = rb.x - sqrtf(d2);
                     if (l < -ph.cut) continue;
-                    // (1 + tanh(2l/eps)) / 2 == 1 / (1 + exp(-4l/eps))
-                    const float pc = __frcp_rn(1.0f + expf(-ph.four_over_eps * l));
+                    // (1 + tanh(2l/eps)) / 2 == 1 / (1 + exp(-4l/eps)) == 1 / (1 + 2^(phi_k2 l)),
+                    // with the hardware's base-2 exponential and reciprocal: the
+                    // rounding of the argument phi_k2 l (|.| <= 23 inside the tail,
+                    // a relative error of at most 23 * 2^-24 in the power) bounds
+                    // the error either way, and both instructions add about an ulp
+                    const float pc = rcp_approx(1.0f + ex2_approx(ph.phi_k2 * l));
                     if (pc > phi[m] || (pc == phi[m] && pc > 0.f && id < best_id[m])) {
                         phi[m] = pc; best[m] = c; best_id[m] = id; rxn[m] = dx; ryn[m] = dy;
                     }
@@ -1270,6 +1287,18 @@ struct PartArgs {
     double *fpart = nullptr;
 };
 
+// v wrapped into [0, n) on a periodic axis: fmod(v, n), plus n when it is
+// negative.  A position moves by less than a period per step, so within
+// (-n, 2n) one subtraction or addition of n gives exactly that result (the
+// difference is representable); fmod takes anything farther, and NaN.
+__host__ __device__ inline double wrap_period(double v, double n) {
+    if (v >= 0.0 && v < n) return v;
+    if (v >= n && v < 2.0 * n) return v - n;
+    if (v < 0.0 && v > -n) return v + n;
+    const double w = fmod(v, n);
+    return w < 0.0 ? w + n : w;
+}
+
 // Moving computational domain (Sec. 3.5): the frame's move at the end of a
 // step, in columns, from the tracked particle's x at the start of that step
 // (minimum image on a periodic x axis): +1 once it is one lattice unit or
@@ -1370,8 +1399,8 @@ __device__ __forceinline__ void particle_forces(const PartArgs &A, int p, int la
             const double dd = sqrt(dx * dx + dy * dy);
             const double f = dd > 0.0 ? 0.5 * (dd + r - P.r[j]) / dd : 0.0;
             double mx = X - f * dx, my = Y - f * dy;
-            if (L.per_x) { mx = fmod(mx, (double)L.nx); if (mx < 0.0) mx += L.nx; }
-            if (L.per_y) { my = fmod(my, (double)L.ny); if (my < 0.0) my += L.ny; }
+            if (L.per_x) mx = wrap_period(mx, (double)L.nx);
+            if (L.per_y) my = wrap_period(my, (double)L.ny);
             int mxi = (int)floor(mx), myi = (int)floor(my);
             mxi = mxi < 0 ? 0 : (mxi > L.nx - 1 ? L.nx - 1 : mxi);
             myi = myi < 0 ? 0 : (myi > L.ny - 1 ? L.ny - 1 : myi);
@@ -1460,8 +1489,8 @@ __device__ __forceinline__ void particle_update(const PartArgs &A, int p, PartSh
             om += tq * iI;
             nX = X + ux;
             nY = Y + uy;
-            if (L.per_x) { nX = fmod(nX, (double)L.nx); if (nX < 0.0) nX += L.nx; }
-            if (L.per_y) { nY = fmod(nY, (double)L.ny); if (nY < 0.0) nY += L.ny; }
+            if (L.per_x) nX = wrap_period(nX, (double)L.nx);
+            if (L.per_y) nY = wrap_period(nY, (double)L.ny);
             P.ux[p] = ux; P.uy[p] = uy; P.omega[p] = om;
             P.theta[p] += om;
         }
@@ -1476,7 +1505,7 @@ __device__ __forceinline__ void particle_update(const PartArgs &A, int p, PartSh
             const int s = frame_move(pc.xin[A.track], A.track_x, L.nx, L.per_x);
             if (s) {
                 nX -= (double)s;
-                if (L.per_x) { nX = fmod(nX, (double)L.nx); if (nX < 0.0) nX += L.nx; }
+                if (L.per_x) nX = wrap_period(nX, (double)L.nx);
             }
         }
     }

@@ -179,7 +179,7 @@ extern "C" int dilbm_step_static(const dilbm_grid *g, double tau, double interfa
     ph.omega = (float)(1.0 / tau);
     ph.kf = (float)(1.0 - 0.5 / tau);
     ph.kforce = g->force_model == DILBM_FORCE_EQ18 ? ph.kf : 1.0f;
-    ph.four_over_eps = (float)(4.0 / interface_width);
+    ph.phi_k2 = (float)(-4.0 / (interface_width * std::log(2.0)));
     ph.cut_d = PHI_CUT_WIDTHS * interface_width;
     ph.cut = (float)ph.cut_d;
     BodyParams bp{};
