@@ -587,7 +587,8 @@ def batch_arm(args):
             "one_at_a_time": {"value": alone_value, "unit": "MLUPS", "steps": k_alone,
                               "speedup_of_batch": value / alone_value},
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
-                         "traffic": None, "peak_kind": peak_kind, "kernel": "sweep_kernel (batched)",
+                         "traffic": measured_traffic(f"batch:{args.storage}:{len(jobs)}x{nodes}"),
+                         "peak_kind": peak_kind, "kernel": "sweep_kernel (batched)",
                          "sweep_ms_per_launch": per_launch, "algorithmic_bytes_per_launch": alg},
             "gpu_launches": int(sum_over_ranks(dist, launches, dev)), "e2e": None, "clocks": clk}
     if rank == 0:

@@ -43,6 +43,7 @@ constexpr int MAXC = 32;      // candidate particles per tile
 constexpr int MAXT = 128;     // tiles one particle's phi tail may reach
 constexpr int NREC = 3;       // float4 records per binned particle
 constexpr int STAGES = 1;     // row segments staged ahead per warp (shared-memory ring depth)
+static_assert(STAGES == 1, "a warp carries one staged segment's periodic-edge values (wrap_load)");
 constexpr int SWEEP_WARPS = 8;   // default rows in flight per block (one row segment per warp)
 constexpr int GUARD = 256;    // elements kept readable before and after a population buffer
 constexpr float PHI_CUT_WIDTHS = 4.0f;   // phi tail kept up to 4 interface widths (phi > 1.1e-7)
@@ -430,6 +431,36 @@ __device__ __forceinline__ void issue_segment(const T *__restrict__ src, const L
     }
 }
 
+// Periodic x: the staged halo of a row's first segment does not hold column
+// nx - 1 (what node 0 streams from in the three directions with c_ix = +1),
+// nor does the stage of its last segment hold column 0 after column nx - 1
+// (what node nx - 1 streams from with c_ix = -1).  When a warp issues such a
+// segment's copy, lanes 0..2 also load the first value (planes 1, 5, 8) and
+// lanes 3..5 the second (planes 3, 6, 7), raw; once the copy has landed,
+// wrap_patch writes them where the pulls look.  wrap_lane_plane gives the
+// plane of the lane's value and whether the segment needs it.
+__device__ __forceinline__ int wrap_lane_plane(const Lattice &L, int tx, int lane) {
+    if (!L.per_x || lane >= 6) return -1;
+    const bool first = tx == 0, last = tx * TILE_W + TILE_W >= L.nx;
+    if (lane < 3) return first ? (lane == 0 ? 1 : (lane == 1 ? 5 : 8)) : -1;
+    return last ? (lane == 3 ? 3 : (lane == 4 ? 6 : 7)) : -1;
+}
+
+template <typename T>
+__device__ __forceinline__ T wrap_load(const T *__restrict__ src, const Lattice &L, int y, int tx, int lane) {
+    const int i = wrap_lane_plane(L, tx, lane);
+    if (i < 0) return T();
+    const T *row = plane_row<T>(src, L, i, y - cyof(i));
+    return row[lane < 3 ? L.nx - 1 : 0];
+}
+
+template <typename T>
+__device__ __forceinline__ void wrap_patch(T *stage, const Lattice &L, int tx, int lane, T v) {
+    constexpr int H = halo_of<T>(), SW = segw_of<T>();
+    const int i = wrap_lane_plane(L, tx, lane);
+    if (i >= 0) stage[i * SW + (lane < 3 ? H - 1 : H + (L.nx - tx * TILE_W))] = v;
+}
+
 template <typename T>
 __device__ __forceinline__ void pull_node_scalar(const T *__restrict__ src, const Lattice &L, int x, int y, float d[9]) {
 #pragma unroll
@@ -724,16 +755,18 @@ __device__ __forceinline__ float rcp_approx(float x) {
 // Slot m (0 or 1) of a node pair.
 __device__ __forceinline__ float &slot(float2 &v, int m) { return m ? v.y : v.x; }
 
-// One row segment (row y, segment tx) of lattice A: wait for its staged rows,
-// then sweep its 128 nodes in two passes of 64 (lane l takes nodes 2l and
-// 2l + 1 of each half, so every store of a pass is one contiguous run per
-// plane), hand the stage to the segment `nxt` (row ny2, segment nx2 of
-// lattice An) once the second pass has read it, and sum the segment's force /
-// torque per candidate particle.  Returns false if the bounded wait gave up.
+// One row segment (row y, segment tx) of lattice A: wait for its staged rows
+// (and write in the periodic-edge values wv, see wrap_load), then sweep its
+// 128 nodes in two passes of 64 (lane l takes nodes 2l and 2l + 1 of each
+// half, so every store of a pass is one contiguous run per plane), hand the
+// stage to the segment `nxt` (row ny2, segment nx2 of lattice An; its edge
+// values go to wv) once the second pass has read it, and sum the segment's
+// force / torque per candidate particle.  Returns false if the bounded wait
+// gave up.
 template <typename T, int MODE, bool EDGES, bool PS = false>
 __device__ __forceinline__ bool sweep_segment(const SweepArgs<T> &A, int y, int tx, T *stage, Ring &ring, int s,
                                               bool has_next, const SweepArgs<T> &An, int ny2, int nx2,
-                                              float4 *crec, int *cid, int lane) {
+                                              float4 *crec, int *cid, T &wv, int lane) {
     constexpr int H = halo_of<T>(), SW = segw_of<T>();
     const Lattice &L = A.L;
     const Physics &ph = A.ph;
@@ -763,8 +796,8 @@ __device__ __forceinline__ bool sweep_segment(const SweepArgs<T> &A, int y, int 
 
     const bool row_edge = EDGES && (south_edge_row(L, y) || north_edge_row(L, y));
     const bool col_edge = EDGES && !L.per_x && (tx == 0 || tx0 + TILE_W >= L.nx);
-    const bool wrap_end = L.per_x && (tx == 0 || tx0 + TILE_W >= L.nx);
-    __syncwarp();   // candidate records visible to the whole warp
+    if (L.per_x && (tx == 0 || tx0 + TILE_W >= L.nx)) wrap_patch<T>(stage, L, tx, lane, wv);
+    __syncwarp();   // candidate records and edge values visible to the whole warp
 
     // lane c < ncand: the segment's force / torque on candidate c so far
     // (first pass, then second pass added)
@@ -783,22 +816,6 @@ __device__ __forceinline__ bool sweep_segment(const SweepArgs<T> &A, int y, int 
             const T *row = stage + i * SW + H + e;
             if (cxof(i) == 0) dk[i] = Storage<T>::lds2(row);
             else dk[i] = make_float2(Storage<T>::lds1(row - cxof(i)), Storage<T>::lds1(row + 1 - cxof(i)));
-        }
-        // periodic x: the row's first node pulls from column nx-1 and its
-        // last node from column 0, which the staged halo does not hold
-        if (wrap_end) {
-#pragma unroll
-            for (int m = 0; m < 2; ++m) {
-                const int xm = x + m;
-                if (xm != 0 && xm != L.nx - 1) continue;
-#pragma unroll
-                for (int i = 0; i < 9; ++i) {
-                    if (cxof(i) == 0) continue;
-                    const T *src_row = plane_row<T>(A.src, L, i, y - cyof(i));
-                    if (cxof(i) == 1 && xm == 0) slot(dk[i], m) = Storage<T>::load1(src_row + (L.nx - 1));
-                    if (cxof(i) == -1 && xm == L.nx - 1) slot(dk[i], m) = Storage<T>::load1(src_row);
-                }
-            }
         }
         // west / east edge nodes of a row that is not itself an edge row take
         // the inner neighbour's (same row) streamed values, from the stage
@@ -821,6 +838,7 @@ __device__ __forceinline__ bool sweep_segment(const SweepArgs<T> &A, int y, int 
             if (has_next) {
                 fence_proxy_async_smem();
                 issue_segment<T>(An.src, An.L, ny2, nx2, stage, &ring.bars[s], lane);
+                wv = wrap_load<T>(An.src, An.L, ny2, nx2, lane);
                 ring.pending |= 1u << s;
             }
         }
@@ -1110,11 +1128,13 @@ sweep_kernel(const __grid_constant__ SweepArgs<T> one)
     int y = gw / L.ntx, tx = gw - (gw / L.ntx) * L.ntx;
     ring.parity = 0;
     ring.pending = 0;
+    T wv = T();         // the staged segment's periodic-edge value (wrap_load)
     {
         int py = y, ptx = tx;
         for (int s = 0; s < STAGES; ++s) {
             if (gw + s * nw < nitems) {
                 issue_segment<T>(one.src, L, py, ptx, sm.stages + s * stage_elems<T>(), &ring.bars[s], lane);
+                wv = wrap_load<T>(one.src, L, py, ptx, lane);
                 ring.pending |= 1u << s;
             }
             advance(py, ptx);
@@ -1134,7 +1154,7 @@ sweep_kernel(const __grid_constant__ SweepArgs<T> one)
         const int s = k % STAGES;
         const bool has_next = item + STAGES * nw < nitems;
         if (!sweep_segment<T, MODE, EDGES, PS>(one, y, tx, sm.stages + s * stage_elems<T>(), ring, s, has_next, one, ay, atx,
-                                           sm.crec, sm.cid, lane)) {
+                                           sm.crec, sm.cid, wv, lane)) {
             timed_out = true;
             break;
         }
@@ -1199,12 +1219,14 @@ sweep_batch_kernel(const __grid_constant__ BatchArgs<T> ba)
     Cursor cur{0, 0, 0, 0}, ahead{0, 0, 0, 0};
     ring.parity = 0;
     ring.pending = 0;
+    T wv = T();         // the staged segment's periodic-edge value (wrap_load)
     for (int s = 0; s < STAGES; ++s) {
         const int it = gw + s * nw;
         if (it < nitems) {
             cursor_seek(ba, ahead, it);
             issue_segment<T>(ba.a[ahead.lat].src, ba.a[ahead.lat].L, ahead.y, ahead.tx,
                              sm.stages + s * stage_elems<T>(), &ring.bars[s], lane);
+            wv = wrap_load<T>(ba.a[ahead.lat].src, ba.a[ahead.lat].L, ahead.y, ahead.tx, lane);
             ring.pending |= 1u << s;
         }
     }
@@ -1221,7 +1243,7 @@ sweep_batch_kernel(const __grid_constant__ BatchArgs<T> ba)
         if (has_next) cursor_seek(ba, ahead, nxt);
         const int nlat = has_next ? ahead.lat : cur.lat;
         if (!sweep_segment<T, MODE, true>(ba.a[cur.lat], cur.y, cur.tx, sm.stages + s * stage_elems<T>(), ring, s,
-                                          has_next, ba.a[nlat], ahead.y, ahead.tx, sm.crec, sm.cid, lane)) {
+                                          has_next, ba.a[nlat], ahead.y, ahead.tx, sm.crec, sm.cid, wv, lane)) {
             timed_out = true;
             break;
         }
