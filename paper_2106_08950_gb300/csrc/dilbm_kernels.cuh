@@ -797,6 +797,24 @@ __device__ __forceinline__ bool sweep_segment(const SweepArgs<T> &A, int y, int 
     const bool row_edge = EDGES && (south_edge_row(L, y) || north_edge_row(L, y));
     const bool col_edge = EDGES && !L.per_x && (tx == 0 || tx0 + TILE_W >= L.nx);
     if (L.per_x && (tx == 0 || tx0 + TILE_W >= L.nx)) wrap_patch<T>(stage, L, tx, lane, wv);
+    // west / east edge nodes of a row that is not itself an edge row: the
+    // non-equilibrium extrapolation from the inner neighbour's streamed values
+    // (same row, staged).  Pull streaming reads each staged value at exactly
+    // one node, so lane 0 (west) and lane 1 (east) write the edge node's
+    // extrapolated populations, in storage form, into the cells that node's
+    // pulls read, and the pulls below pick them up.  (For nx >= 3 the cells
+    // one edge writes and those the other reads are distinct.)
+    if (col_edge && !row_edge && lane < 2) {
+        const int xm = lane == 0 ? 0 : L.nx - 1;
+        const int e = xm - tx0;
+        if (e >= 0 && e < TILE_W) {
+            float dn[9], ev[9];
+            staged_pull9<T>(L, stage, e + (lane == 0 ? 1 : -1), dn);
+            extrapolate(L, lane == 0 ? WEST : EAST, dn, ev);
+#pragma unroll
+            for (int i = 0; i < 9; ++i) Storage<T>::store1(stage + i * SW + H + e - cxof(i), to_store<T>(L, i, ev[i]));
+        }
+    }
     __syncwarp();   // candidate records and edge values visible to the whole warp
 
     // lane c < ncand: the segment's force / torque on candidate c so far
@@ -816,20 +834,6 @@ __device__ __forceinline__ bool sweep_segment(const SweepArgs<T> &A, int y, int 
             const T *row = stage + i * SW + H + e;
             if (cxof(i) == 0) dk[i] = Storage<T>::lds2(row);
             else dk[i] = make_float2(Storage<T>::lds1(row - cxof(i)), Storage<T>::lds1(row + 1 - cxof(i)));
-        }
-        // west / east edge nodes of a row that is not itself an edge row take
-        // the inner neighbour's (same row) streamed values, from the stage
-        if (col_edge && !row_edge) {
-#pragma unroll
-            for (int m = 0; m < 2; ++m) {
-                const int xm = x + m;
-                if (xm != 0 && xm != L.nx - 1) continue;
-                float dn[9], ev[9];
-                staged_pull9<T>(L, stage, e + m + (xm == 0 ? 1 : -1), dn);
-                extrapolate(L, xm == 0 ? WEST : EAST, dn, ev);
-#pragma unroll
-                for (int i = 0; i < 9; ++i) slot(dk[i], m) = to_store<T>(L, i, ev[i]);
-            }
         }
         // the segment's last reads of the stage are done: recycle it for the
         // segment STAGES items ahead
