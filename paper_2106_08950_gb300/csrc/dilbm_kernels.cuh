@@ -1371,7 +1371,15 @@ struct PartCopies {
 };
 
 // (A) Hydrodynamic force and torque (Eqs. 18-19) from the sweep's partials,
-// and the particle-particle repulsion (Eq. 28), summed over the warp.
+// and the particle-particle repulsion (Eq. 28), summed over the warp.  Both
+// sums start from the particle's tile entries, which each lane loads once
+// (entry k = lane + 32 q in register q); the first requests of the repulsion
+// search (its first tile's count and first ids) go out before the force sum,
+// so that the two chains of dependent loads overlap.
+constexpr int PSLOT_REGS = MAXT / 32;   // tile entries per lane
+static_assert(MAXT % 32 == 0 && MAXC >= 4, "tile entries are spread over whole warps");
+constexpr int CONTACT_PREFETCH = 4;     // ids of the first tile requested early
+
 __device__ __forceinline__ void particle_forces(const PartArgs &A, int p, int lane, PartShared &sh) {
     const Lattice &L = A.L;
     const Particles &P = A.P;
@@ -1383,13 +1391,43 @@ __device__ __forceinline__ void particle_forces(const PartArgs &A, int p, int la
     const float *xfin = pc.xfin, *yfin = pc.yfin;
     const double X = xin[p], Y = yin[p], r = P.r[p];
 
-    // ---- 1. hydrodynamic force and torque
-    double fx = 0.0, fy = 0.0, tq = 0.0;
     const int nk = bin_in.npslot[p];
-    for (int e = lane; e < nk * TILE_H; e += 32) {
+    int tsl[PSLOT_REGS];
+#pragma unroll
+    for (int q = 0; q < PSLOT_REGS; ++q) {
+        const int k = lane + 32 * q;
+        tsl[q] = k < nk ? bin_in.pslot[(long long)p * MAXT + k] : -1;
+    }
+    // the repulsion search's first tile: its count and first ids (slots of
+    // the tile, in bounds; used only below the count)
+    const int t0 = tsl[0] >= 0 ? tsl[0] / MAXC : -1;
+    int cnt0 = 0, jpre[CONTACT_PREFETCH];
+    if (t0 >= 0) {
+        cnt0 = bin_in.count[t0];
+#pragma unroll
+        for (int s = 0; s < CONTACT_PREFETCH; ++s) jpre[s] = bin_in.ids[t0 * MAXC + s];
+    } else {
+#pragma unroll
+        for (int s = 0; s < CONTACT_PREFETCH; ++s) jpre[s] = 0;
+    }
+
+    // ---- 1. hydrodynamic force and torque: lane l adds entries e = l, l + 32,
+    // ... (tile entry e / TILE_H, row e % TILE_H) in that order
+    double fx = 0.0, fy = 0.0, tq = 0.0;
+    const int ne = nk * TILE_H;
+#pragma unroll 2
+    for (int base = 0; base < ne; base += 32) {
+        const int e = base + lane;
         const int k = e / TILE_H, row = e - k * TILE_H;
-        const int ts = bin_in.pslot[(long long)p * MAXT + k];
-        if (ts < 0) continue;
+        // entry k sits in lane k % 32, register k / 32 = base / (32 TILE_H)
+        // (the same for the whole warp in one iteration)
+        const int q = base / (32 * TILE_H);
+        int src = tsl[0];
+#pragma unroll
+        for (int qq = 1; qq < PSLOT_REGS; ++qq)
+            if (q == qq) src = tsl[qq];
+        const int ts = __shfl_sync(0xffffffffu, src, k & 31);
+        if (e >= ne || ts < 0) continue;
         const int ty = (ts / MAXC) / L.ntx + A.ty_lo;
         if (ty * TILE_H + row >= L.ny) continue;
         const float4 v = partial[(long long)ts * TILE_H + row];
@@ -1402,15 +1440,21 @@ __device__ __forceinline__ void particle_forces(const PartArgs &A, int p, int la
     // within a tile the pairs are added in increasing partner id.
     double cx = 0.0, cy = 0.0;
     const float xf = xfin[p], yf = yfin[p], rf = (float)r;
-    for (int k = lane; k < nk; k += 32) {
-        const int ts = bin_in.pslot[(long long)p * MAXT + k];
+#pragma unroll
+    for (int q = 0; q < PSLOT_REGS; ++q) {
+        if (lane + 32 * q >= nk) break;
+        const int ts = tsl[q];
         if (ts < 0) continue;
         const int t = ts / MAXC;
-        int n = bin_in.count[t];
+        int n = q == 0 ? cnt0 : bin_in.count[t];
         n = n > MAXC ? MAXC : n;
         uint32_t contact = 0;
         for (int sl = 0; sl < n; ++sl) {
-            const int j = bin_in.ids[t * MAXC + sl];
+            int j;
+            if (q == 0 && sl < CONTACT_PREFETCH)
+                j = sl == 0 ? jpre[0] : (sl == 1 ? jpre[1] : (sl == 2 ? jpre[2] : jpre[3]));
+            else
+                j = bin_in.ids[t * MAXC + sl];
             if (j == p) continue;
             float dxf = xf - xfin[j], dyf = yf - yfin[j];
             if (L.per_x) { if (dxf >= 0.5f * L.nx) dxf -= L.nx; else if (dxf < -0.5f * L.nx) dxf += L.nx; }
@@ -1470,18 +1514,35 @@ __device__ __forceinline__ void particle_forces(const PartArgs &A, int p, int la
     }
 }
 
+// The particle state (B) reads, loaded at the start of the kernel so that
+// its latency passes while the warps sum their forces.
+struct PartState {
+    double X, Y, r, ux, uy, om, rho_s, theta;
+    int fixed;
+};
+
+__device__ __forceinline__ PartState load_state(const PartArgs &A, int p) {
+    const Particles &P = A.P;
+    const PartCopies pc(A);
+    PartState st;
+    st.X = pc.xin[p]; st.Y = pc.yin[p]; st.r = P.r[p];
+    st.ux = P.ux[p]; st.uy = P.uy[p]; st.om = P.omega[p];
+    st.rho_s = P.rho_s[p]; st.theta = P.theta[p]; st.fixed = P.fixed[p];
+    return st;
+}
+
 // (B) One thread per particle: wall repulsion (Eq. 29), the rigid-body
 // update (Eqs. 22-24), the frame move, the position copies for the next step,
 // and what the binning needs (velocity splits, the tiles the reach covers).
-__device__ __forceinline__ void particle_update(const PartArgs &A, int p, PartShared &sh) {
+__device__ __forceinline__ void particle_update(const PartArgs &A, int p, PartShared &sh, const PartState &st) {
     const Lattice &L = A.L;
     const Physics &ph = A.ph;
     const Particles &P = A.P;
     const BodyParams &bp = A.bp;
     const PartCopies pc(A);
-    const double X = pc.xin[p], Y = pc.yin[p], r = P.r[p];
+    const double X = st.X, Y = st.Y, r = st.r;
     double nX = X, nY = Y;
-    double ux = P.ux[p], uy = P.uy[p], om = P.omega[p];
+    double ux = st.ux, uy = st.uy, om = st.om;
 
     if (A.integrate) {
         const double fx = sh.fx, fy = sh.fy, tq = sh.tq;
@@ -1503,13 +1564,13 @@ __device__ __forceinline__ void particle_update(const PartArgs &A, int p, PartSh
             cy += sc * dy;
         }
         // ---- 3. rigid-body update
-        if (!P.fixed[p]) {
+        if (!st.fixed) {
             // two FP64 divisions instead of four: the buoyancy-reduced weight
             // (1 - rho_f / rho_s) m g is (rho_s - rho_f) pi r^2 g
             const double area = 3.14159265358979323846 * r * r;
-            const double m = P.rho_s[p] * area;
+            const double m = st.rho_s * area;
             const double im = 1.0 / m, iI = 1.0 / (0.5 * m * r * r);
-            const double wgt = (P.rho_s[p] - bp.rho_f) * area;      // buoyancy-reduced weight / g
+            const double wgt = (st.rho_s - bp.rho_f) * area;        // buoyancy-reduced weight / g
             ux += (fx + cx + wgt * bp.gx) * im;
             uy += (fy + cy + wgt * bp.gy) * im;
             om += tq * iI;
@@ -1518,7 +1579,7 @@ __device__ __forceinline__ void particle_update(const PartArgs &A, int p, PartSh
             if (L.per_x) nX = wrap_period(nX, (double)L.nx);
             if (L.per_y) nY = wrap_period(nY, (double)L.ny);
             P.ux[p] = ux; P.uy[p] = uy; P.omega[p] = om;
-            P.theta[p] += om;
+            P.theta[p] = st.theta + om;
         }
         A.force[3 * p] = fx; A.force[3 * p + 1] = fy; A.force[3 * p + 2] = tq;
         A.fcol[2 * p] = cx; A.fcol[2 * p + 1] = cy;
@@ -1628,6 +1689,14 @@ particles_kernel(const __grid_constant__ PartArgs one, const PartArgs *__restric
     int p = 0;
     const PartArgs *A = locate(blockIdx.x * PART_WARPS + w, p);
     const int phase = BATCH ? 0 : one.phase;       // (uniform over the launch)
+    // (B)'s lanes: their particle and its state, requested now
+    int q = 0;
+    const PartArgs *B = nullptr;
+    PartState st{};
+    if (phase != 1 && w == 0 && lane < PART_WARPS) {
+        B = locate(blockIdx.x * PART_WARPS + lane, q);
+        if (B) st = load_state(*B, q);
+    }
     if (A && A->integrate && phase != 2) particle_forces(*A, p, lane, sh[w]);
     if (phase == 1) {
         if (A && A->integrate && lane == 0) {
@@ -1641,11 +1710,7 @@ particles_kernel(const __grid_constant__ PartArgs one, const PartArgs *__restric
         sh[w].fx = o[0]; sh[w].fy = o[1]; sh[w].tq = o[2]; sh[w].cx = o[3]; sh[w].cy = o[4];
     }
     __syncthreads();
-    if (w == 0 && lane < PART_WARPS) {
-        int q = 0;
-        const PartArgs *B = locate(blockIdx.x * PART_WARPS + lane, q);
-        if (B) particle_update(*B, q, sh[lane]);
-    }
+    if (B) particle_update(*B, q, sh[lane], st);
     __syncthreads();
     if (A) particle_bin(*A, p, lane, sh[w]);
 }
