@@ -1452,8 +1452,9 @@ int shape_candidates(Occ occupancy, std::vector<SweepShape> *out) {
 // Time every candidate in TUNE_ROUNDS interleaved rounds of `reps` launches
 // each (after one untimed launch) on `stream`; *best receives the candidate
 // with the smallest median round time (interleaving spreads clock and
-// neighbour noise over all candidates alike).
-constexpr int TUNE_ROUNDS = 3;
+// neighbour noise over all candidates alike).  The full-occupancy shapes of
+// the large sweeps differ by 1-2 %, so the median is taken over 7 rounds.
+constexpr int TUNE_ROUNDS = 7;
 
 template <typename Launch>
 int time_shapes(cudaStream_t stream, int reps, const std::vector<SweepShape> &cands, Launch launch, SweepShape *best) {

@@ -800,11 +800,13 @@ __device__ __forceinline__ bool sweep_segment(const SweepArgs<T> &A, int y, int 
     // west / east edge nodes of a row that is not itself an edge row: the
     // non-equilibrium extrapolation from the inner neighbour's streamed values
     // (same row, staged).  Pull streaming reads each staged value at exactly
-    // one node, so lane 0 (west) and lane 1 (east) write the edge node's
-    // extrapolated populations, in storage form, into the cells that node's
-    // pulls read, and the pulls below pick them up.  (For nx >= 3 the cells
-    // one edge writes and those the other reads are distinct.)
-    if (col_edge && !row_edge && lane < 2) {
+    // one node, so in FP32 storage lane 0 (west) and lane 1 (east) write the
+    // edge node's extrapolated populations into the cells that node's pulls
+    // read, and the pulls below pick them up.  (For nx >= 3 the cells one
+    // edge writes and those the other reads are distinct.)  16-bit storage
+    // would round them on the way; there the passes replace the pulled values.
+    constexpr bool EDGE_IN_STAGE = std::is_same<T, float>::value;
+    if (EDGE_IN_STAGE && col_edge && !row_edge && lane < 2) {
         const int xm = lane == 0 ? 0 : L.nx - 1;
         const int e = xm - tx0;
         if (e >= 0 && e < TILE_W) {
@@ -834,6 +836,20 @@ __device__ __forceinline__ bool sweep_segment(const SweepArgs<T> &A, int y, int 
             const T *row = stage + i * SW + H + e;
             if (cxof(i) == 0) dk[i] = Storage<T>::lds2(row);
             else dk[i] = make_float2(Storage<T>::lds1(row - cxof(i)), Storage<T>::lds1(row + 1 - cxof(i)));
+        }
+        if constexpr (!EDGE_IN_STAGE) {
+            if (col_edge && !row_edge) {
+#pragma unroll
+                for (int m = 0; m < 2; ++m) {
+                    const int xm = x + m;
+                    if (xm != 0 && xm != L.nx - 1) continue;
+                    float dn[9], ev[9];
+                    staged_pull9<T>(L, stage, e + m + (xm == 0 ? 1 : -1), dn);
+                    extrapolate(L, xm == 0 ? WEST : EAST, dn, ev);
+#pragma unroll
+                    for (int i = 0; i < 9; ++i) slot(dk[i], m) = to_store<T>(L, i, ev[i]);
+                }
+            }
         }
         // the segment's last reads of the stage are done: recycle it for the
         // segment STAGES items ahead
