@@ -1480,10 +1480,14 @@ int time_shapes(cudaStream_t stream, int reps, const std::vector<SweepShape> &ca
     cudaEventDestroy(e1);
     if (e != cudaSuccess) return cuda_fail(e, "autotune launch");
     float best_ms = 0.f;
+    const bool log = std::getenv("DILBM_TUNE_LOG") != nullptr;
     for (size_t k = 0; k < cands.size(); ++k) {
         float *m = &ms[k * TUNE_ROUNDS];
         std::sort(m, m + TUNE_ROUNDS);
         const float med = m[TUNE_ROUNDS / 2];
+        if (log)
+            std::fprintf(stderr, "dilbm autotune: warps %d blocks/SM %d: median %.4f ms per %d launches\n",
+                         cands[k].warps, cands[k].blocks_per_sm, med, reps);
         if (k == 0 || med < best_ms) {
             best_ms = med;
             *best = cands[k];
