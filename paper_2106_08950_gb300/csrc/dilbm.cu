@@ -84,7 +84,34 @@ struct dilbm_ctx {
     bool strip_open = false;               // between dilbm_strip_begin and dilbm_strip_end
     void *owned[40] = {};
     int nowned = 0;
+    // dilbm_set_particles packs into pinned host memory, so its copies run
+    // asynchronously; up_done marks when the last upload's copies have read it
+    void *up_stage = nullptr;
+    cudaEvent_t up_done = nullptr;
+    // dilbm_forces with the state: one device block in the staging layout
+    // (force 3 np, fcol 2 np, x, y, r, ux, uy, omega, theta, rho_s as doubles,
+    // then fixed and the error word as ints), read back by one copy
+    double *readback = nullptr;
 };
+
+// Gathers dilbm_forces' outputs into the readback block (layout above).
+__global__ void readback_kernel(double *__restrict__ out, const double *__restrict__ force,
+                                const double *__restrict__ fcol, const double *__restrict__ x,
+                                const double *__restrict__ y, const double *__restrict__ rest,
+                                const int *__restrict__ fixed, const int *__restrict__ err, int np) {
+    const long long nd = 13LL * np;
+    int *oi = reinterpret_cast<int *>(out + nd);
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < nd + np + 1;
+         i += (long long)gridDim.x * blockDim.x) {
+        if (i < 3LL * np) out[i] = force[i];
+        else if (i < 5LL * np) out[i] = fcol[i - 3LL * np];
+        else if (i < 6LL * np) out[i] = x[i - 5LL * np];
+        else if (i < 7LL * np) out[i] = y[i - 6LL * np];
+        else if (i < nd) out[i] = rest[i - 7LL * np];
+        else if (i < nd + np) oi[i - nd] = fixed[i - nd];
+        else oi[np] = *err;
+    }
+}
 
 namespace {
 
@@ -267,8 +294,20 @@ int upload_particles(dilbm_ctx *c, const dilbm_particle *p, int np) {
     int rc = check_reach(c->ph.cut_d, p, np);
     if (rc) return rc;
     if ((rc = size_cover_tables(c, p, np))) return rc;
-    std::vector<double> h(8 * (size_t)np);
-    std::vector<int> fx(np);
+    // pinned staging: x, y, then r, ux, uy, omega, theta, rho_s (one device
+    // slice), as doubles, then fixed as ints; reused once the previous
+    // upload's copies have read it
+    if (!c->up_stage) {
+        if (cudaHostAlloc(&c->up_stage, (sizeof(double) * 8 + sizeof(int)) * (size_t)np, cudaHostAllocDefault) != cudaSuccess) {
+            c->up_stage = nullptr;
+            return fail(DILBM_ERR_OOM, "pinned staging for the particle upload");
+        }
+        DILBM_CUDA(cudaEventCreateWithFlags(&c->up_done, cudaEventDisableTiming));
+    } else {
+        DILBM_CUDA(cudaEventSynchronize(c->up_done));
+    }
+    double *h = static_cast<double *>(c->up_stage);
+    int *fx = reinterpret_cast<int *>(h + 8 * (size_t)np);
     for (int k = 0; k < np; ++k) {
         h[0 * np + k] = p[k].x; h[1 * np + k] = p[k].y; h[2 * np + k] = p[k].r;
         h[3 * np + k] = p[k].ux; h[4 * np + k] = p[k].uy; h[5 * np + k] = p[k].omega;
@@ -276,13 +315,13 @@ int upload_particles(dilbm_ctx *c, const dilbm_particle *p, int np) {
         fx[k] = p[k].fixed ? 1 : 0;
     }
     const int cur = c->cur;
-    DILBM_CUDA(cudaMemcpyAsync(c->P.x[cur], h.data(), sizeof(double) * np, cudaMemcpyHostToDevice, c->stream));
-    DILBM_CUDA(cudaMemcpyAsync(c->P.y[cur], h.data() + np, sizeof(double) * np, cudaMemcpyHostToDevice, c->stream));
+    DILBM_CUDA(cudaMemcpyAsync(c->P.x[cur], h, sizeof(double) * np, cudaMemcpyHostToDevice, c->stream));
+    DILBM_CUDA(cudaMemcpyAsync(c->P.y[cur], h + np, sizeof(double) * np, cudaMemcpyHostToDevice, c->stream));
     // r, ux, uy, omega, theta, rho_s are consecutive slices of one allocation
-    DILBM_CUDA(cudaMemcpyAsync(c->P.r, h.data() + 2 * np, sizeof(double) * 6 * np, cudaMemcpyHostToDevice, c->stream));
-    DILBM_CUDA(cudaMemcpyAsync(c->P.fixed, fx.data(), sizeof(int) * np, cudaMemcpyHostToDevice, c->stream));
+    DILBM_CUDA(cudaMemcpyAsync(c->P.r, h + 2 * np, sizeof(double) * 6 * np, cudaMemcpyHostToDevice, c->stream));
+    DILBM_CUDA(cudaMemcpyAsync(c->P.fixed, fx, sizeof(int) * np, cudaMemcpyHostToDevice, c->stream));
+    DILBM_CUDA(cudaEventRecord(c->up_done, c->stream));
     DILBM_CUDA(cudaMemsetAsync(c->bins[cur].count, 0, sizeof(int) * c->ntiles, c->stream));
-    // (no wait: a copy from pageable memory has staged the source when it returns)
     return launch_particles(c, 0);
 }
 
@@ -856,15 +895,25 @@ int dilbm_forces(dilbm_ctx *c, double *force, double *fcol, dilbm_particle *stat
     if (!h) return fail(DILBM_ERR_OOM, "pinned staging for dilbm_forces");
     double *hf = h, *hc = h + 3 * np, *hs = h + 5 * np;
     int *fx = reinterpret_cast<int *>(h + 13 * np), *herr = fx + np;
-    DILBM_CUDA(cudaMemcpyAsync(hf, c->force, sizeof(double) * 3 * np, cudaMemcpyDeviceToHost, c->stream));
-    if (fcol) DILBM_CUDA(cudaMemcpyAsync(hc, c->fcol, sizeof(double) * 2 * np, cudaMemcpyDeviceToHost, c->stream));
+    const size_t block_bytes = sizeof(double) * 13 * np + sizeof(int) * (np + 1);
     if (state) {
-        DILBM_CUDA(cudaMemcpyAsync(hs, c->P.x[c->cur], sizeof(double) * np, cudaMemcpyDeviceToHost, c->stream));
-        DILBM_CUDA(cudaMemcpyAsync(hs + np, c->P.y[c->cur], sizeof(double) * np, cudaMemcpyDeviceToHost, c->stream));
-        DILBM_CUDA(cudaMemcpyAsync(hs + 2 * np, c->P.r, sizeof(double) * 6 * np, cudaMemcpyDeviceToHost, c->stream));
-        DILBM_CUDA(cudaMemcpyAsync(fx, c->P.fixed, sizeof(int) * np, cudaMemcpyDeviceToHost, c->stream));
+        // everything in one copy, gathered on the device
+        if (!c->readback) {
+            void *q = nullptr;
+            if (cudaMalloc(&q, block_bytes) != cudaSuccess) return fail(DILBM_ERR_OOM, "device readback block for dilbm_forces");
+            c->readback = static_cast<double *>(q);
+        }
+        const int threads = 256, blocks = (int)((block_bytes / sizeof(int) + threads - 1) / threads);
+        readback_kernel<<<blocks < 4 * c->num_sms ? blocks : 4 * c->num_sms, threads, 0, c->stream>>>(
+            c->readback, c->force, c->fcol, c->P.x[c->cur], c->P.y[c->cur], c->P.r, c->P.fixed, c->err, (int)np);
+        DILBM_CUDA(cudaGetLastError());
+        c->launches += 1;
+        DILBM_CUDA(cudaMemcpyAsync(h, c->readback, block_bytes, cudaMemcpyDeviceToHost, c->stream));
+    } else {
+        DILBM_CUDA(cudaMemcpyAsync(hf, c->force, sizeof(double) * 3 * np, cudaMemcpyDeviceToHost, c->stream));
+        if (fcol) DILBM_CUDA(cudaMemcpyAsync(hc, c->fcol, sizeof(double) * 2 * np, cudaMemcpyDeviceToHost, c->stream));
+        DILBM_CUDA(cudaMemcpyAsync(herr, c->err, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
     }
-    DILBM_CUDA(cudaMemcpyAsync(herr, c->err, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
     DILBM_CUDA(cudaStreamSynchronize(c->stream));
     c->sticky |= *herr;
     std::memcpy(force, hf, sizeof(double) * 3 * np);
@@ -1036,6 +1085,9 @@ void dilbm_destroy(dilbm_ctx *c) {
     for (int k = 0; k < c->nowned; ++k) cudaFree(c->owned[k]);
     if (c->cover) cudaFree(c->cover);
     for (cudaEvent_t e : c->ev) cudaEventDestroy(e);
+    if (c->up_done) cudaEventDestroy(c->up_done);
+    if (c->up_stage) cudaFreeHost(c->up_stage);
+    if (c->readback) cudaFree(c->readback);
     delete c;
 }
 
