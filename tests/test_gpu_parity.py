@@ -333,6 +333,41 @@ def test_checkpoint_resume_bitwise(stream):
     assert np.array_equal(a.populations(), b.populations())
 
 
+def test_host_coupled_loop(stream):
+    # A host-coupled particle loop, as the end-to-end bench runs it: every
+    # step reads the forces and state back, a host-side controller changes
+    # the state (it damps one disc's velocity and nudges another's spin), and
+    # uploads it again.  The uploads reuse one pinned staging buffer, and the
+    # state comes back in one gathered copy.  The oracle takes the same
+    # controller; the readback of forces alone gives the same bits.
+    prob = moving_particles()
+    g = D.Simulation(prob, stream=stream)
+    o = O.OracleSim(prob, phi_cutoff=PAR.oracle_cutoff(prob))
+    steps = 40
+    for k in range(steps):
+        Fg, Fcg, Sg = g.forces()
+        F_only = np.zeros_like(Fg)
+        g.forces_into(F_only)
+        assert np.array_equal(F_only, Fg)
+        _, _, So = o.forces()
+        parts = []
+        for q, row_g, row_o in zip(prob.particles, Sg, So):
+            ok, e = PAR.compare_state(row_g[None, :], row_o[None, :])
+            assert ok, (k, e)
+            parts.append(row_g)
+        ctrl = [np.array(r, dtype=np.float64) for r in parts]
+        ctrl[0][3] *= 0.9                        # damp disc 0's x velocity
+        ctrl[1][5] += 1e-4                       # spin disc 1 up
+        newp = [W.Particle(*r[:8], fixed=q.fixed) for r, q in zip(ctrl, prob.particles)]
+        g.set_particles(newp)
+        o.set_particles(newp)
+        if k == steps - 1:
+            o.pre = PAR.oracle_pre(o)        # the last step's inputs
+        g.step(1)
+        o.step(1)
+    assert_forces(g, o, prob)
+
+
 def test_runs_are_deterministic(stream):
     prob = W.periodic_suspension(n=512, count=32, seed=9)
     r = []
