@@ -103,19 +103,19 @@ def test_batch_rejects_mixed_storage(stream):
 
 def test_full_size_batch_workload_against_oracle(stream):
     # The benchmark's batch workload itself (64 uneven lattices, about 19 M
-    # nodes, 1-32 discs each), autotuned as bench.py does, for 4 steps: every
+    # nodes, 1-32 discs each), autotuned as bench.py does, for 50 steps: every
     # member's forces and particle state, and 20k sampled nodes of each,
     # against the oracle (same 4-width phi cutoff).
     jobs = W.batch_lattices(seed=4)
     members = [D.Simulation(j, stream=stream) for j in jobs]
     batch = D.Batch(members)
     batch.autotune(reps=2)
-    batch.step(4)
+    batch.step(50)
     batch.sync()
     rng = np.random.default_rng(1)
     for k, (p, m) in enumerate(zip(jobs, members)):
         o = O.OracleSim(p, phi_cutoff=4 * p.eps)
-        o.step(3)
+        o.step(49)
         pre = PAR.oracle_pre(o)
         o.step(1)
         Fg, _, Sg = m.forces()
