@@ -824,8 +824,11 @@ __device__ __forceinline__ bool sweep_segment(const SweepArgs<T> &A, int y, int 
     float sgx = 0.f, sgy = 0.f, sgt = 0.f;
     unsigned badmax = 0u;
 
+    // a row's last segment may end within its first half: its second pass
+    // would hold no node (no store, no force share), so it is not run
+    const int npass = tx0 + TILE_W / 2 < L.nx ? 2 : 1;
 #pragma unroll 1
-    for (int pass = 0; pass < 2; ++pass) {
+    for (int pass = 0; pass < npass; ++pass) {
         const int e = pass * (TILE_W / 2) + 2 * lane;    // the pair's first node within the segment
         const int x = tx0 + e;
 
@@ -853,7 +856,7 @@ __device__ __forceinline__ bool sweep_segment(const SweepArgs<T> &A, int y, int 
         }
         // the segment's last reads of the stage are done: recycle it for the
         // segment STAGES items ahead
-        if (pass == 1) {
+        if (pass == npass - 1) {
             __syncwarp();
             if (has_next) {
                 fence_proxy_async_smem();
