@@ -117,6 +117,8 @@ namespace {
 
 template <typename Tp>
 int dev_alloc(dilbm_ctx *c, Tp **p, size_t count) {
+    if (c->nowned >= (int)(sizeof(c->owned) / sizeof(c->owned[0])))
+        return fail(DILBM_ERR_OOM, "too many device allocations for one context");
     void *q = nullptr;
     cudaError_t e = cudaMalloc(&q, count * sizeof(Tp) > 0 ? count * sizeof(Tp) : 16);
     if (e != cudaSuccess) return cuda_fail(e, "cudaMalloc");
