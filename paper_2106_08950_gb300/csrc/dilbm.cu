@@ -115,14 +115,23 @@ __global__ void readback_kernel(double *__restrict__ out, const double *__restri
 
 namespace {
 
+// Record device memory the context frees at destroy (frees q and fails when
+// the table is full).
+int keep_owned(dilbm_ctx *c, void *q) {
+    if (c->nowned >= (int)(sizeof(c->owned) / sizeof(c->owned[0]))) {
+        cudaFree(q);
+        return fail(DILBM_ERR_OOM, "too many device allocations for one context");
+    }
+    c->owned[c->nowned++] = q;
+    return DILBM_OK;
+}
+
 template <typename Tp>
 int dev_alloc(dilbm_ctx *c, Tp **p, size_t count) {
-    if (c->nowned >= (int)(sizeof(c->owned) / sizeof(c->owned[0])))
-        return fail(DILBM_ERR_OOM, "too many device allocations for one context");
     void *q = nullptr;
     cudaError_t e = cudaMalloc(&q, count * sizeof(Tp) > 0 ? count * sizeof(Tp) : 16);
     if (e != cudaSuccess) return cuda_fail(e, "cudaMalloc");
-    c->owned[c->nowned++] = q;
+    if (int rc = keep_owned(c, q)) return rc;
     *p = static_cast<Tp *>(q);
     return DILBM_OK;
 }
@@ -706,7 +715,7 @@ static int create_ctx(const dilbm_grid *g, dilbm_lattice lattice, double tau, do
         void *q = nullptr;
         cudaError_t e = cudaMalloc(&q, pop_elems * c->elem);
         if (e != cudaSuccess) return bail(cuda_fail(e, "cudaMalloc populations"));
-        c->owned[c->nowned++] = q;
+        if (int rc = keep_owned(c, q)) return bail(rc);
         c->buf[b] = static_cast<char *>(q) + GUARD * c->elem;
         e = cudaMemsetAsync(q, 0, pop_elems * c->elem, c->stream);
         if (e != cudaSuccess) return bail(cuda_fail(e, "cudaMemsetAsync"));
@@ -738,7 +747,7 @@ static int create_ctx(const dilbm_grid *g, dilbm_lattice lattice, double tau, do
             void *q = nullptr;
             cudaError_t e2 = cudaMalloc(&q, row_elems * c->elem);
             if (e2 != cudaSuccess) return bail(cuda_fail(e2, "cudaMalloc halo rows"));
-            c->owned[c->nowned++] = q;
+            if (int rc = keep_owned(c, q)) return bail(rc);
             e2 = cudaMemsetAsync(q, 0, row_elems * c->elem, c->stream);
             if (e2 != cudaSuccess) return bail(cuda_fail(e2, "cudaMemsetAsync"));
             (k < 2 ? c->xsend[k] : c->xrecv[k - 2]) = static_cast<char *>(q) + GUARD * c->elem;
@@ -1012,7 +1021,7 @@ int dilbm_fields(dilbm_ctx *c, float *rho, float *ux, float *uy, float *phi, int
     if (!c->fields) {
         void *q = nullptr;
         DILBM_CUDA(cudaMalloc(&q, sizeof(float) * 4 * n));
-        c->owned[c->nowned++] = q;
+        if (int rc = keep_owned(c, q)) return rc;
         c->fields = (float *)q;
     }
     fo = FieldsOut{c->fields, c->fields + n, c->fields + 2 * n, c->fields + 3 * n};
@@ -1029,7 +1038,7 @@ static int ensure_pops(dilbm_ctx *c) {
     if (c->pops) return DILBM_OK;
     void *q = nullptr;
     DILBM_CUDA(cudaMalloc(&q, sizeof(double) * 9 * (size_t)c->L.nx * c->L.ny));
-    c->owned[c->nowned++] = q;
+    if (int rc = keep_owned(c, q)) return rc;
     c->pops = (double *)q;
     return DILBM_OK;
 }
