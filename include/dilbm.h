@@ -271,7 +271,16 @@ int dilbm_fields(dilbm_ctx *ctx, float *rho, float *ux, float *uy, float *phi, i
 int dilbm_get_populations(dilbm_ctx *ctx, double *f);
 int dilbm_set_populations(dilbm_ctx *ctx, const double *f);
 
-/* Replace the particle state (host array of the np given at create). */
+/*
+ * Replace the particle state: host array of the np given at create, checked
+ * as at create (inside the lattice, positive finite radius and density,
+ * finite velocities, phi tail within the per-particle tile map).  The state is
+ * copied into the context's pinned staging before the call returns, so the
+ * caller may reuse the array at once; the upload and the re-binning for the
+ * next step are queued on the stream (asynchronous).  Errors: INVALID_ARG
+ * (count differs from create, or a particle fails a check; nothing changes),
+ * OOM, CUDA.
+ */
 int dilbm_set_particles(dilbm_ctx *ctx, const dilbm_particle *particles, int np);
 
 /* Wait for queued work; return the first sticky device error, else DILBM_OK. */
