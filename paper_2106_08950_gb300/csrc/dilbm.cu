@@ -299,11 +299,12 @@ int size_cover_tables(dilbm_ctx *c, const dilbm_particle *p, int np) {
 }
 
 int upload_particles(dilbm_ctx *c, const dilbm_particle *p, int np) {
+    // every check before any state changes
+    int rc = check_reach(c->ph.cut_d, p, np);
+    if (rc) return rc;
     const int wx = c->L.wrap_x, wy = c->L.wrap_y;
     set_wrap_flags(c, p, np);
     if (c->L.wrap_x != wx || c->L.wrap_y != wy) drop_graphs(c);
-    int rc = check_reach(c->ph.cut_d, p, np);
-    if (rc) return rc;
     if ((rc = size_cover_tables(c, p, np))) return rc;
     // pinned staging: x, y, then r, ux, uy, omega, theta, rho_s (one device
     // slice), as doubles, then fixed as ints; reused once the previous
