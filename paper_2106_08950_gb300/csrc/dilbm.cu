@@ -1501,14 +1501,19 @@ namespace {
 std::mutex g_tune_mu;
 std::map<std::tuple<int, int, int, long long, long long>, SweepShape> g_tune;
 
+// Candidate shapes, each with the warps it keeps resident per SM.
 template <typename Occ>
-int shape_candidates(Occ occupancy, std::vector<SweepShape> *out) {
+int shape_candidates(Occ occupancy, std::vector<SweepShape> *out, std::vector<int> *warps_per_sm) {
     for (int w : SHAPE_WARPS) {
         int per_sm = 0;
         cudaError_t e = occupancy(SweepShape{w, 0}, &per_sm);
         if (e != cudaSuccess) return cuda_fail(e, "sweep occupancy");
         out->push_back(SweepShape{w, 0});
-        if (per_sm >= 2) out->push_back(SweepShape{w, per_sm / 2});
+        warps_per_sm->push_back(w * per_sm);
+        if (per_sm >= 2) {
+            out->push_back(SweepShape{w, per_sm / 2});
+            warps_per_sm->push_back(w * (per_sm / 2));
+        }
     }
     return DILBM_OK;
 }
@@ -1517,11 +1522,16 @@ int shape_candidates(Occ occupancy, std::vector<SweepShape> *out) {
 // each (after one untimed launch) on `stream`; *best receives the candidate
 // with the smallest median round time (interleaving spreads clock and
 // neighbour noise over all candidates alike).  The full-occupancy shapes of
-// the large sweeps differ by 1-2 %, so the median is taken over 7 rounds.
+// the large sweeps differ by 1-2 %, so the median is taken over 7 rounds, and
+// candidates within TUNE_TIE of the fastest count as tied: the one keeping the
+// most warps resident per SM wins (a step runs the particle kernel between
+// sweeps, and there the shape with more warps measured faster).
 constexpr int TUNE_ROUNDS = 7;
+constexpr float TUNE_TIE = 0.01f;
 
 template <typename Launch>
-int time_shapes(cudaStream_t stream, int reps, const std::vector<SweepShape> &cands, Launch launch, SweepShape *best) {
+int time_shapes(cudaStream_t stream, int reps, const std::vector<SweepShape> &cands, const std::vector<int> &warps_per_sm,
+                Launch launch, SweepShape *best) {
     cudaEvent_t e0 = nullptr, e1 = nullptr;
     DILBM_CUDA(cudaEventCreate(&e0));
     cudaError_t e = cudaEventCreate(&e1);
@@ -1543,20 +1553,26 @@ int time_shapes(cudaStream_t stream, int reps, const std::vector<SweepShape> &ca
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
     if (e != cudaSuccess) return cuda_fail(e, "autotune launch");
-    float best_ms = 0.f;
     const bool log = std::getenv("DILBM_TUNE_LOG") != nullptr;
+    std::vector<float> med(cands.size());
+    float best_ms = 0.f;
     for (size_t k = 0; k < cands.size(); ++k) {
         float *m = &ms[k * TUNE_ROUNDS];
         std::sort(m, m + TUNE_ROUNDS);
-        const float med = m[TUNE_ROUNDS / 2];
+        med[k] = m[TUNE_ROUNDS / 2];
         if (log)
-            std::fprintf(stderr, "dilbm autotune: warps %d blocks/SM %d: median %.4f ms per %d launches\n",
-                         cands[k].warps, cands[k].blocks_per_sm, med, reps);
-        if (k == 0 || med < best_ms) {
-            best_ms = med;
-            *best = cands[k];
-        }
+            std::fprintf(stderr, "dilbm autotune: warps %d blocks/SM %d (%d warps per SM): median %.4f ms per %d launches\n",
+                         cands[k].warps, cands[k].blocks_per_sm, warps_per_sm[k], med[k], reps);
+        if (k == 0 || med[k] < best_ms) best_ms = med[k];
     }
+    int pick = -1;
+    for (size_t k = 0; k < cands.size(); ++k) {
+        if (med[k] > best_ms * (1.0f + TUNE_TIE)) continue;
+        if (pick < 0 || warps_per_sm[k] > warps_per_sm[pick] ||
+            (warps_per_sm[k] == warps_per_sm[pick] && med[k] < med[pick]))
+            pick = (int)k;
+    }
+    *best = cands[pick];
     return DILBM_OK;
 }
 
@@ -1611,12 +1627,13 @@ int dilbm_autotune(dilbm_ctx *c, int reps, int *warps, int *blocks_per_sm) {
     SweepShape best = c->shape;
     if (!tuned(key, &best)) {
         std::vector<SweepShape> cands;
+        std::vector<int> wps;
         int rc = shape_candidates([&](const SweepShape &sh, int *per_sm) { return step_sweep(c, sh, true, per_sm); },
-                                  &cands);
+                                  &cands, &wps);
         if (rc) return rc;
         // each launch sweeps the current state into the other buffer: what
         // the next step writes anyway
-        rc = time_shapes(c->stream, reps, cands, [&](const SweepShape &sh) { return step_sweep(c, sh); }, &best);
+        rc = time_shapes(c->stream, reps, cands, wps, [&](const SweepShape &sh) { return step_sweep(c, sh); }, &best);
         c->launches += (long long)cands.size() * (reps + 1) * TUNE_ROUNDS;
         if (rc) return rc;
         remember(key, best);
@@ -1655,6 +1672,7 @@ int dilbm_batch_autotune(dilbm_batch *b, int reps, int *warps, int *blocks_per_s
         if (stale && (rc = prepare_batch(b))) return rc;
         const int phase = (int)(b->done & 1);
         std::vector<SweepShape> cands;
+        std::vector<int> wps;
         rc = shape_candidates(
             [&](const SweepShape &sh, int *per_sm) {
                 switch (b->storage) {
@@ -1663,9 +1681,9 @@ int dilbm_batch_autotune(dilbm_batch *b, int reps, int *warps, int *blocks_per_s
                 default: return launch_batch_sweep<__nv_bfloat16>(*static_cast<const BatchArgs<__nv_bfloat16> *>(b->sweep_params[0][0]), sh, 1, b->stream, true, per_sm);
                 }
             },
-            &cands);
+            &cands, &wps);
         if (rc) return rc;
-        rc = time_shapes(b->stream, reps, cands, [&](const SweepShape &sh) { return batch_sweep(b, phase, sh); }, &best);
+        rc = time_shapes(b->stream, reps, cands, wps, [&](const SweepShape &sh) { return batch_sweep(b, phase, sh); }, &best);
         b->launches += (long long)cands.size() * (reps + 1) * TUNE_ROUNDS * (long long)b->sweep_params[phase].size();
         if (rc) return rc;
         remember(key, best);
